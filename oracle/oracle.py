@@ -1,0 +1,236 @@
+"""ctypes binding of the FP64 C oracle (``nlbm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg use it; the CUDA library never does.  The C source is
+compiled here with the host compiler (gcc, OpenMP) into ``oracle/_build``.
+
+Parameters are passed as a plain dict with the keys the workload generator
+produces: nx, ny, n_phases, model ('A' or 'B'), model_a_n, eps, mobility,
+rho[N], mu[N] (dynamic viscosities), sigma[N][N], wall_x, wall_y.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nlbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+MAXN = 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class params_struct(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("n_phases", ctypes.c_int32), ("model", ctypes.c_int32),
+        ("wall_x", ctypes.c_int32), ("wall_y", ctypes.c_int32),
+        ("solve_all", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("model_a_n", ctypes.c_double), ("eps", ctypes.c_double),
+        ("mobility", ctypes.c_double),
+        ("rho", ctypes.c_double * MAXN), ("mu", ctypes.c_double * MAXN),
+        ("sigma", ctypes.c_double * (MAXN * MAXN)),
+    ]
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle into a shared library (idempotent, mtime-checked)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def oracle_lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build_oracle())
+            P = ctypes.POINTER
+            d = ctypes.c_double
+            lib.or_create.restype = ctypes.c_void_p
+            lib.or_create.argtypes = [P(params_struct)]
+            lib.or_destroy.argtypes = [ctypes.c_void_p]
+            lib.or_set_phi.argtypes = [ctypes.c_void_p, P(d)]
+            lib.or_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]
+            lib.or_get_moments.argtypes = [ctypes.c_void_p, P(d), P(d), P(d)]
+            lib.or_phase_mass.argtypes = [ctypes.c_void_p, P(d)]
+            lib.or_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, P(d)]
+            lib.or_steps_done.restype = ctypes.c_longlong
+            lib.or_steps_done.argtypes = [ctypes.c_void_p]
+            lib.or_field_grad.argtypes = [P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, P(d)]
+            lib.or_field_lap.argtypes = lib.or_field_grad.argtypes
+            lib.or_point_source.argtypes = [P(params_struct), P(d), P(d), P(d)]
+            lib.or_point_chempot.argtypes = [P(params_struct), P(d), P(d), P(d)]
+            lib.or_mrt_matrices.argtypes = [P(d), P(d)]
+            lib.or_phase_feq.argtypes = [d, d, d, P(d)]
+            lib.or_phase_src.argtypes = [d, d, d, d, P(d)]
+            lib.or_flow_geq.argtypes = [d, d, d, d, d, d, d, P(d)]
+            lib.or_flow_force.argtypes = [d, d, d, P(d), P(d)]
+            lib.or_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(p: dict, solve_all: bool = False) -> params_struct:
+    s = params_struct()
+    N = int(p["n_phases"])
+    s.nx, s.ny, s.n_phases = int(p["nx"]), int(p["ny"]), N
+    s.model = {"A": 0, "B": 1}[p["model"]]
+    s.wall_x, s.wall_y = int(bool(p.get("wall_x", 0))), int(bool(p.get("wall_y", 0)))
+    s.solve_all = int(bool(solve_all))
+    s.model_a_n = float(p.get("model_a_n", 1.0))
+    s.eps, s.mobility = float(p["eps"]), float(p["mobility"])
+    sig = np.asarray(p["sigma"], dtype=np.float64).reshape(N, N)
+    for a in range(N):
+        s.rho[a] = float(p["rho"][a])
+        s.mu[a] = float(p["mu"][a])
+        for b in range(N):
+            s.sigma[a * MAXN + b] = float(sig[a, b])
+    return s
+
+
+class OracleSim:
+    """One FP64 oracle simulation.  ``phi0`` holds phases 1..N-1 as
+    [N-1, ny, nx]; phase N is 1 - sum."""
+
+    def __init__(self, p: dict, phi0: np.ndarray, solve_all: bool = False, threads: int = 0):
+        self.lib = oracle_lib()
+        self.p = dict(p)
+        self.N, self.nx, self.ny = int(p["n_phases"]), int(p["nx"]), int(p["ny"])
+        self.threads = threads
+        self._ps = make_params(p, solve_all)
+        self.h = self.lib.or_create(ctypes.byref(self._ps))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+        phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        assert phi0.shape == (self.N - 1, self.ny, self.nx), phi0.shape
+        self.lib.or_set_phi(self.h, _dp(phi0))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or_destroy(h)
+            self.h = None
+
+    def step(self, n: int):
+        self.lib.or_step(self.h, int(n), int(self.threads))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.or_steps_done(self.h))
+
+    def moments(self):
+        phi = np.empty((self.N, self.ny, self.nx))
+        u = np.empty((2, self.ny, self.nx))
+        P = np.empty((self.ny, self.nx))
+        self.lib.or_get_moments(self.h, _dp(phi), _dp(u), _dp(P))
+        return phi, u, P
+
+    def phase_mass(self) -> np.ndarray:
+        m = np.empty(self.N)
+        self.lib.or_phase_mass(self.h, _dp(m))
+        return m
+
+    def field(self, name: str) -> np.ndarray:
+        N, ny, nx = self.N, self.ny, self.nx
+        which, shape = {
+            "R": (0, (N, 2, ny, nx)), "mphi": (1, (2, ny, nx)), "muphi": (2, (N, ny, nx)),
+            "F": (3, (2, ny, nx)), "grad": (4, (N, 2, ny, nx)), "lap": (5, (N, ny, nx)),
+        }[name]
+        out = np.empty(shape)
+        self.lib.or_get_field(self.h, which, _dp(out))
+        return out
+
+
+# ---------------------------------------------------------------- field pins
+
+def field_grad(chi: np.ndarray, wall_x=False, wall_y=False) -> np.ndarray:
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    ny, nx = chi.shape
+    out = np.empty((2, ny, nx))
+    oracle_lib().or_field_grad(_dp(chi), nx, ny, int(wall_x), int(wall_y), _dp(out))
+    return out
+
+
+def field_lap(chi: np.ndarray, wall_x=False, wall_y=False) -> np.ndarray:
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    ny, nx = chi.shape
+    out = np.empty((ny, nx))
+    oracle_lib().or_field_lap(_dp(chi), nx, ny, int(wall_x), int(wall_y), _dp(out))
+    return out
+
+
+def point_source(p: dict, phi: np.ndarray, grad: np.ndarray) -> np.ndarray:
+    N = int(p["n_phases"])
+    ps = make_params({**p, "nx": 1, "ny": 1})
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    grad = np.ascontiguousarray(grad, dtype=np.float64).reshape(N, 2)
+    R = np.empty((N, 2))
+    oracle_lib().or_point_source(ctypes.byref(ps), _dp(phi), _dp(grad), _dp(R))
+    return R
+
+
+def point_chempot(p: dict, phi: np.ndarray, lap: np.ndarray) -> np.ndarray:
+    N = int(p["n_phases"])
+    ps = make_params({**p, "nx": 1, "ny": 1})
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    lap = np.ascontiguousarray(lap, dtype=np.float64)
+    mu = np.empty(N)
+    oracle_lib().or_point_chempot(ctypes.byref(ps), _dp(phi), _dp(lap), _dp(mu))
+    return mu
+
+
+def mrt_matrices():
+    M = np.empty((9, 9))
+    Mi = np.empty((9, 9))
+    oracle_lib().or_mrt_matrices(_dp(M), _dp(Mi))
+    return M, Mi
+
+
+def phase_feq(phi, ux, uy):
+    out = np.empty(9)
+    oracle_lib().or_phase_feq(phi, ux, uy, _dp(out))
+    return out
+
+
+def phase_src(dtx, dty, Rx, Ry):
+    out = np.empty(9)
+    oracle_lib().or_phase_src(dtx, dty, Rx, Ry, _dp(out))
+    return out
+
+
+def flow_geq(P, rho0, rho, ux, uy, mx, my):
+    out = np.empty(9)
+    oracle_lib().or_flow_geq(P, rho0, rho, ux, uy, mx, my, _dp(out))
+    return out
+
+
+def flow_force(ugr, Fx, Fy, M2F):
+    M2F = np.ascontiguousarray(np.asarray(M2F, dtype=np.float64).reshape(4))
+    out = np.empty(9)
+    oracle_lib().or_flow_force(ugr, Fx, Fy, _dp(M2F), _dp(out))
+    return out
+
+
+def max_threads() -> int:
+    return int(oracle_lib().or_max_threads())

@@ -1,0 +1,179 @@
+"""Seeded synthetic workloads shaped like the paper's test problems.
+
+This module holds only initial conditions and parameter draws; it contains
+none of the lattice Boltzmann arithmetic, so the CUDA library and the FP64
+oracle can both be fed from it without sharing any of the method.
+
+Every workload is a pair ``(params, phi0)``:
+
+* ``params`` -- dict with nx, ny, n_phases, model ('A'/'B'), model_a_n, eps,
+  mobility, rho[N], mu[N] (dynamic viscosities), sigma[N][N] (symmetric,
+  zero diagonal), wall_x, wall_y;
+* ``phi0`` -- float64 array [N-1, ny, nx] with the volume fractions of
+  phases 1..N-1; phase N is 1 minus their sum (the paper solves only N-1
+  phase equations, Sec. 4).
+
+Interface profiles follow the static-droplet initialisation of Sec. 4.1,
+Eq. (30): phi = 0.5 + 0.5 tanh((R - r) / (eps/2)), with r the minimum-image
+distance on a periodic axis.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+SEED = 2306
+
+
+def _axis_dist(coord: np.ndarray, c: float, n: int, periodic: bool) -> np.ndarray:
+    d = coord - c
+    if periodic:
+        d = (d + n / 2.0) % n - n / 2.0
+    return d
+
+
+def disk(nx: int, ny: int, cx: float, cy: float, R: float, eps: float,
+         periodic_x: bool = True, periodic_y: bool = True) -> np.ndarray:
+    """tanh disk of radius R centred at node coordinates (cx, cy), Eq. (30)."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    dx = _axis_dist(x, cx, nx, periodic_x)
+    dy = _axis_dist(y, cy, ny, periodic_y)
+    r = np.sqrt(dx * dx + dy * dy)
+    return 0.5 + 0.5 * np.tanh((R - r) / (eps / 2.0))
+
+
+def flat_band(nx: int, ny: int, y0: float, y1: float, eps: float) -> np.ndarray:
+    """Band y0 < y < y1 (periodic in y) with the equilibrium profile
+    0.5 + 0.5 tanh(2 d / eps) of Sec. 2.1, d the signed distance to the
+    nearer interface (positive inside the band)."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    c, h = 0.5 * (y0 + y1), 0.5 * (y1 - y0)
+    d = h - np.abs(_axis_dist(y, c, ny, True))
+    return 0.5 + 0.5 * np.tanh(2.0 * d / eps)
+
+
+def base_params(nx, ny, N, model="B", model_a_n=1.0, eps=4.0, mobility=0.1,
+                rho=None, mu=None, sigma=0.01, wall_x=False, wall_y=False) -> dict:
+    rho = np.ones(N) if rho is None else np.asarray(rho, dtype=np.float64)
+    mu = rho / 6.0 if mu is None else np.asarray(mu, dtype=np.float64)
+    if np.isscalar(sigma):
+        sig = np.full((N, N), float(sigma))
+        np.fill_diagonal(sig, 0.0)
+    else:
+        sig = np.asarray(sigma, dtype=np.float64).reshape(N, N)
+    return dict(nx=int(nx), ny=int(ny), n_phases=int(N), model=model,
+                model_a_n=float(model_a_n), eps=float(eps), mobility=float(mobility),
+                rho=[float(v) for v in rho], mu=[float(v) for v in mu],
+                sigma=sig.tolist(), wall_x=bool(wall_x), wall_y=bool(wall_y))
+
+
+def droplets_64(model="B", model_a_n=1.0):
+    """Three-phase droplets on a 64x64 periodic lattice (small CPU case):
+    N = 3, eps = 4, all densities 1, relaxation time 1 for every phase
+    (nu = 1/6, mu_p = rho_p / 6), mobility 0.1, all sigma = 0.01; phase 2 a
+    disk R = 12 at (32, 32), phase 3 a disk R = 8 at (14, 14), phase 1 the
+    rest."""
+    nx = ny = 64
+    p = base_params(nx, ny, 3, model=model, model_a_n=model_a_n, eps=4.0, mobility=0.1,
+                    rho=[1.0, 1.0, 1.0], sigma=0.01)
+    d2 = disk(nx, ny, 32, 32, 12, 4.0)
+    d3 = disk(nx, ny, 14, 14, 8, 4.0)
+    phi0 = np.stack([1.0 - d2 - d3, d2])
+    return p, phi0
+
+
+def random_disks(nx, ny, N, n_disks, rmin, rmax, seed=SEED, model="B", model_a_n=1.0,
+                 eps=4.0, mobility=0.1, rho=None, nu_range=(0.01, 0.1),
+                 sigma_range=(0.005, 0.02), max_tries=200000):
+    """Non-overlapping tanh disks in a matrix of phase 1 on a periodic lattice.
+
+    Radii U[rmin, rmax], labels U{2..N}, periodic gap >= R_i + R_j + 2 eps
+    (rejection sampling), kinematic viscosities U[nu_range] per phase
+    (mu_p = rho_p nu_p), pairwise sigma U[sigma_range] per unordered pair.
+    With N = 5 the default densities are {1, 2, 5, 10, 1}."""
+    rng = np.random.default_rng(seed)
+    if rho is None:
+        rho = [1.0, 2.0, 5.0, 10.0, 1.0][:N] if N <= 5 else list(np.linspace(1, 10, N))
+    rho = np.asarray(rho, dtype=np.float64)
+    nu = rng.uniform(nu_range[0], nu_range[1], size=N)
+    sig = np.zeros((N, N))
+    for a in range(N):
+        for b in range(a + 1, N):
+            sig[a, b] = sig[b, a] = rng.uniform(sigma_range[0], sigma_range[1])
+    disks = []
+    tries = 0
+    while len(disks) < n_disks and tries < max_tries:
+        tries += 1
+        R = rng.uniform(rmin, rmax)
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        ok = True
+        for (ox, oy, oR, _) in disks:
+            dx = _axis_dist(np.array(cx), ox, nx, True)
+            dy = _axis_dist(np.array(cy), oy, ny, True)
+            if np.hypot(dx, dy) < R + oR + 2 * eps:
+                ok = False
+                break
+        if ok:
+            disks.append((cx, cy, R, int(rng.integers(2, N + 1))))
+    if len(disks) < n_disks:
+        raise RuntimeError(f"placed only {len(disks)} of {n_disks} disks")
+    fields = np.zeros((N + 1, ny, nx))
+    for (cx, cy, R, lab) in disks:
+        fields[lab] += disk(nx, ny, cx, cy, R, eps)
+    phi = np.empty((N, ny, nx))
+    phi[0] = 1.0 - fields[2:N + 1].sum(axis=0)
+    for lab in range(2, N + 1):
+        phi[lab - 1] = fields[lab]
+    p = base_params(nx, ny, N, model=model, model_a_n=model_a_n, eps=eps, mobility=mobility,
+                    rho=rho, mu=rho * nu, sigma=sig)
+    p["disks"] = len(disks)
+    return p, phi[:N - 1].copy()
+
+
+def disks_2048(model="B", model_a_n=1.0, seed=SEED):
+    """Five-phase disk suspension on a 2048x2048 periodic lattice: 200 disks,
+    radii U[10, 40], labels U{2..5}, phase 1 the matrix, densities
+    {1, 2, 5, 10, 1}, kinematic viscosities U[0.01, 0.1], sigma U[0.005, 0.02],
+    eps = 4, mobility 0.1."""
+    return random_disks(2048, 2048, 5, 200, 10.0, 40.0, seed=seed, model=model,
+                        model_a_n=model_a_n)
+
+
+def disks_256(model="B", model_a_n=1.0, seed=SEED):
+    """The 2048^2 five-phase suspension cut to 256x256: 25 disks with radii
+    U[6, 12] (the full-size radii scaled by 1/8 would fall below the
+    interface width), same parameter draws."""
+    return random_disks(256, 256, 5, 25, 6.0, 12.0, seed=seed, model=model,
+                        model_a_n=model_a_n)
+
+
+def random_smooth(nx, ny, N, seed=SEED, model="B", model_a_n=1.0, eps=4.0,
+                  wall_x=False, wall_y=False, n_disks=None):
+    """Small ragged-size test lattice with a few disks of random phases
+    (no gap constraint beyond rejection of exact overlap of centres)."""
+    rng = np.random.default_rng(seed)
+    n_disks = n_disks if n_disks is not None else max(2, (nx * ny) // 300)
+    fields = np.zeros((N + 1, ny, nx))
+    for _ in range(n_disks):
+        R = rng.uniform(3.0, max(3.5, min(nx, ny) / 4.0))
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        lab = int(rng.integers(2, N + 1))
+        fields[lab] = np.maximum(fields[lab], disk(nx, ny, cx, cy, R, eps,
+                                                   not wall_x, not wall_y))
+    tot = fields[2:].sum(axis=0)
+    scale = np.where(tot > 1.0, 1.0 / np.maximum(tot, 1e-300), 1.0)
+    fields[2:] *= scale
+    phi = np.empty((N, ny, nx))
+    phi[0] = 1.0 - fields[2:N + 1].sum(axis=0)
+    for lab in range(2, N + 1):
+        phi[lab - 1] = fields[lab]
+    rho = rng.uniform(1.0, 5.0, size=N)
+    nu = rng.uniform(0.02, 0.1, size=N)
+    sig = np.zeros((N, N))
+    for a in range(N):
+        for b in range(a + 1, N):
+            sig[a, b] = sig[b, a] = rng.uniform(0.005, 0.02)
+    p = base_params(nx, ny, N, model=model, model_a_n=model_a_n, eps=eps, mobility=0.1,
+                    rho=rho, mu=rho * nu, sigma=sig, wall_x=wall_x, wall_y=wall_y)
+    return p, phi[:N - 1].copy()
