@@ -1,0 +1,344 @@
+"""Benchmark: device-timed MLUPS of the fused N-phase lattice Boltzmann step
+and its fraction of the HBM roofline.
+
+Workload (one GPU): the 2048x2048 periodic five-phase disk suspension
+(200 disks, radii U[10, 40], densities {1, 2, 5, 10, 1}, eps = 4, mobility
+0.1, Model B unless --model A).  One step = every phase set and the flow set
+advanced one time step = one launch of the fused step kernel.  The
+population buffers (604 MB each) are larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--model A|B] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (weak scaling, no collective on the data path); rank 0 prints one
+JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (rank 0
+only), on a 256x256 cut of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N-phase LBM MLUPS & % HBM roofline: plain FP32 vs BF16/batched/adjoint forms"
+WORKLOAD = "2048x2048 periodic, N=5, 200 disks (seed 2306), eps=4, M=0.1"
+
+
+def bytes_per_lup(N: int) -> int:
+    """Algorithmic HBM bytes of one lattice update, FP32 storage: each stored
+    value read once and written once -- 9(N-1) phase + 8 flow populations,
+    (N-1) phi + 2 u + 2 m_phi of the previous step."""
+    return 8 * (9 * (N - 1) + 8 + (N - 1) + 4)
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_06983_gb300", "csrc")
+    for name in ("step_kernel.cuh", "nlbm_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(model: str):
+    """DRAM bytes per lattice update of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_model{model}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_digest") != kernel_sources_digest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_lup"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def oracle_sample(model: str, steps: int, warmup: int, cut: int = 512):
+    """FP64 oracle on a cut x cut corner of the workload; returns (MLUPS, cores, seconds)."""
+    from oracle.oracle import OracleSim, max_threads
+    from paper_2306_06983_gb300 import workloads as W
+    p, phi0 = W.disks_2048(model)
+    q = dict(p, nx=cut, ny=cut)
+    o = OracleSim(q, np.ascontiguousarray(phi0[:, :cut, :cut]))
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return cut * cut * steps / dt / 1e6, max_threads(), dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.oracle import build_oracle
+    build_oracle()
+    steps = max(1, args.steps)
+    cut = 256
+    mlups, cores, dt = oracle_sample(args.model, steps, args.warmup, cut)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + f", Model {args.model}; {cut}x{cut} cut on host cores",
+                   "nx": cut, "ny": cut, "n_phases": 5, "model": args.model},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{steps} time steps of a {cut}x{cut} cut of the 2048x2048 "
+                                   f"N=5 workload, FP64 oracle, OpenMP"},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2306_06983_gb300 import workloads as W
+    from paper_2306_06983_gb300.nlbm import Simulation
+
+    if args.lattice:
+        lx, ly = args.lattice
+        n_disks = max(1, int(round(200 * lx * ly / 2048 ** 2)))
+        p, phi0 = W.random_disks(lx, ly, 5, n_disks, 10.0, 40.0, model=args.model)
+        workload = f"{lx}x{ly} periodic, N=5, {n_disks} disks (seed 2306), eps=4, M=0.1"
+    else:
+        p, phi0 = W.disks_2048(args.model)
+        workload = WORKLOAD
+    N, nx, ny = p["n_phases"], p["nx"], p["ny"]
+    lups = nx * ny
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = Simulation(p, stream=stream)
+        if args.tile:
+            sim.set_tile(*args.tile)
+        sim.set_phi(phi0.astype(np.float32))
+        sim.step(args.warmup)
+        stream.synchronize()
+
+        # ---------------------------------------------- device-timed region
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = sim.kernel_launches
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clocks:
+            t_start.record(stream)
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                sim.step(1)
+                ev[k][1].record(stream)
+            t_end.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches = sim.kernel_launches - launches0
+        total_ms = t_start.elapsed_time(t_end)
+        per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+        mass = sim.phase_mass(allow_diverged=True)
+        tile = list(sim.get_tile())
+        sim.close()
+
+        # ------------------------------------------- end to end, host buffers
+        phi_host = torch.from_numpy(phi0.astype(np.float32)).pin_memory()
+        out_phi = torch.empty((N, ny, nx), dtype=torch.float32).pin_memory()
+        out_u = torch.empty((2, ny, nx), dtype=torch.float32).pin_memory()
+        out_p = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+        sim2 = Simulation(p, stream=stream)
+        if args.tile:
+            sim2.set_tile(*args.tile)
+        stream.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_l0 = sim2.kernel_launches
+        t0 = time.perf_counter()
+        e0.record(stream)
+        sim2.set_phi_host(phi_host)
+        sim2.step(args.steps)
+        sim2.moments_host(out_phi, out_u, out_p)
+        e2e_mass = sim2.phase_mass(allow_diverged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_launches = sim2.kernel_launches - e2e_l0
+        sim2.close()
+
+    total_s = total_ms / 1e3
+    if world > 1:
+        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    mlups = world * lups * args.steps / total_s / 1e6
+    avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
+    bpl = bytes_per_lup(N)
+    achieved = bpl * lups / avg_launch_s / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic_bpl = measured_traffic(args.model)
+    line = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload + f", Model {args.model}", "nx": nx, "ny": ny,
+                   "n_phases": N, "model": args.model, "tile": tile,
+                   "l2": f"inputs larger than L2 ({36 * nx * ny * 4 / 1e6:.0f} MB per phase-population "
+                         f"buffer vs 129 MB L2); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": (round(traffic_bpl * lups) if traffic_bpl else None),
+                     "kernel": f"step_kernel<NS=4, MODEL={args.model}>",
+                     "algorithmic_bytes_per_lup": bpl,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "avg_launch_ms": round(avg_launch_s * 1e3, 5)},
+        "e2e": {"value": round(world * lups * args.steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(4 * (N - 1) * lups / args.steps),
+                "d2h_bytes_per_step": round((4 * (N + 3) * lups + 8 * N) / args.steps),
+                "seconds": round(e2e_s, 4), "gpu_launches": e2e_launches,
+                "path": "nlbm_set_phi_host (pinned) + nlbm_step + nlbm_get_moments_host + "
+                        "nlbm_phase_mass"},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "mass_after": [float(v) for v in mass],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        from oracle.oracle import build_oracle
+        build_oracle()
+        mlups_cpu, cores, dt = oracle_sample(args.model, args.cpu_steps, 1)
+        line["cpu_baseline"] = {
+            "value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{args.cpu_steps} time steps of a 512x512 cut of the workload, FP64 "
+                      f"oracle, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--model", choices=["A", "B"], default="B")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--tile", type=int, nargs=2, default=None, metavar=("TX", "TY"))
+    ap.add_argument("--lattice", type=int, nargs=2, default=None, metavar=("NX", "NY"),
+                    help="profiling aid: a disk suspension of this size instead of 2048x2048")
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

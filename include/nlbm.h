@@ -1,0 +1,176 @@
+/*
+ * nlbm.h -- C ABI of the GB300 (sm_103a) N-phase conservative Allen-Cahn
+ * lattice Boltzmann library.
+ *
+ * The library advances the consistent and conservative lattice Boltzmann
+ * method for immiscible N-phase flow of Zhan, Liu, Chai & Shi (arXiv
+ * 2306.06983): N-1 phase-field distribution sets solving the conservative
+ * Allen-Cahn equation (Sec. 2.1, Eq. (1), with the Model A source of Eq. (2)
+ * or the Model B source of Eqs. (3)-(4)) and one D2Q9 set for the consistent
+ * incompressible Navier-Stokes equations (Sec. 2.2, Eqs. (10)-(17)), both
+ * with the moment-space MRT collision of Sec. 3-4 (Eqs. (18)-(28)).
+ *
+ * Conventions for every call:
+ *  - All functions return an nlbm_status; none throws, none aborts.  After a
+ *    non-OK status, nlbm_last_error() describes the cause.
+ *  - Field arrays are single precision, structure of arrays, row-major:
+ *    element (c, y, x) of a [C][ny][nx] array is at c*ny*nx + y*nx + x.
+ *  - "dev_" pointers are device memory of the GPU that is current when
+ *    nlbm_create() is called; "host_" pointers are host memory (pinned or
+ *    pageable).  The caller owns all of them; the library never frees caller
+ *    memory and keeps no pointer to it after a call returns, except the
+ *    workspace given to nlbm_create().
+ *  - Asynchronous calls are enqueued on the stream given to nlbm_create() and
+ *    return before the GPU work finishes; calls marked "synchronizes" wait
+ *    for that stream.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef NLBM_H
+#define NLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NLBM_OK = 0,
+    NLBM_EINVAL = 1,     /* invalid argument or parameter set */
+    NLBM_ENOMEM = 2,     /* workspace too small / host allocation failed */
+    NLBM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    NLBM_ENOTSUP = 4,    /* valid but not supported by this build */
+    NLBM_EDIVERGED = 5   /* a phase field became non-finite or left [-0.5, 1.5] */
+} nlbm_status;
+
+/* Boundary type of one lattice axis.  NLBM_BC_WALL is the half-way
+ * bounce-back wall of Sec. 4 (no-flux for the phase fields, no-slip for the
+ * velocity), placed half a spacing outside the first and last node; the
+ * stencils of Eq. (27) see mirrored phase fields there. */
+typedef enum { NLBM_BC_PERIODIC = 0, NLBM_BC_WALL = 1 } nlbm_bc;
+
+/* Allen-Cahn source term: Model A is Eq. (2) (Lagrange multiplier with
+ * exponent n), Model B is Eqs. (3)-(4) (pairwise normals). */
+typedef enum { NLBM_MODEL_A = 0, NLBM_MODEL_B = 1 } nlbm_model;
+
+/* Storage precision of the distribution functions.  Only NLBM_STORE_F32 is
+ * implemented; the others return NLBM_ENOTSUP. */
+typedef enum { NLBM_STORE_F32 = 0, NLBM_STORE_BF16 = 1, NLBM_STORE_F16 = 2 } nlbm_storage;
+
+/* The problem statement, in lattice units (dx = dt = 1, c_s^2 = 1/3). */
+typedef struct nlbm_params {
+    int32_t nx, ny;        /* lattice size, >= 1 each (>= 4 along a wall axis) */
+    int32_t bc_x, bc_y;    /* nlbm_bc per axis */
+    int32_t n_phases;      /* N, 2..8; phases 1..N-1 are solved, phase N is
+                              1 - sum (Sec. 4) */
+    int32_t model;         /* nlbm_model */
+    double model_a_n;      /* Model A exponent n > 0 (Eq. (2)); ignored by B */
+    double eps;            /* interface thickness epsilon > 0 (Eq. (2)) */
+    double mobility;       /* M > 0; tau_f = 0.5 + M / c_s^2 (Eq. (20)) */
+    const double *rho;     /* [N] phase densities > 0 (Eq. (11)), host memory */
+    const double *mu;      /* [N] dynamic viscosities > 0 (Eq. (12)), host */
+    const double *sigma;   /* [N*N] pairwise surface tensions, symmetric,
+                              zero diagonal, > 0 off it (Eq. (15)), host */
+    double gx, gy;         /* body acceleration; must be 0 (else ENOTSUP) */
+    int32_t storage;       /* nlbm_storage */
+    int32_t reserved;      /* must be 0 */
+} nlbm_params;
+
+typedef struct nlbm_sim nlbm_sim;
+
+/* Bytes of device workspace one simulation with these parameters needs.
+ * Validates the parameters (EINVAL / ENOTSUP as nlbm_create would).  Host
+ * only, no GPU call. */
+nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes);
+
+/* Create a simulation.  dev_workspace: caller-owned device memory of at least
+ * nlbm_workspace_bytes() bytes, 256-byte aligned, that must stay valid until
+ * nlbm_destroy(); the library lays out the populations (two copies each, pull
+ * streaming), the auxiliary fields and reduction scratch in it.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * later call is enqueued.  The parameters are copied; the caller may free
+ * p->rho, p->mu, p->sigma afterwards.  The state is undefined until
+ * nlbm_set_phi().  Errors: EINVAL (bad parameters, NULL pointers, unaligned
+ * or too small workspace), ENOTSUP (gravity, reduced storage), ENOMEM (host
+ * handle allocation). */
+nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t workspace_bytes,
+                        void *cuda_stream, nlbm_sim **out);
+
+/* Set the initial phase fields and reset the state to the paper's initial
+ * condition: dev_phi [N-1][ny][nx] holds phases 1..N-1 (phase N = 1 - sum),
+ * the fluid is at rest (u = 0, P = 0), the phase populations are the
+ * equilibria w_i phi_p of Eq. (19) and the flow populations those of
+ * Eq. (22) with P = 0.  Resets the step counter.  Asynchronous. */
+nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi);
+
+/* As nlbm_set_phi() with host_phi [N-1][ny][nx] in host memory; the copy is
+ * enqueued on the simulation's stream (synchronizes when host_phi is
+ * pageable). */
+nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi);
+
+/* Advance nsteps >= 0 time steps (Sec. 3: one fused pull-stream, stencil
+ * (Eq. (27)), source (Eqs. (2)-(4)), surface-tension (Eqs. (16)-(17)),
+ * macroscopic (Eqs. (25)) and MRT collision (Eqs. (18)-(24), (28)) pass per
+ * step).  Asynchronous; one kernel launch per step. */
+nlbm_status nlbm_step(nlbm_sim *s, int64_t nsteps);
+
+/* Macroscopic fields of the most recent step (the values the last step
+ * computed before its collision; after nlbm_set_phi() and no step: the
+ * initial phi, u = 0, P = 0).  dev_phi [N][ny][nx] (all N phases),
+ * dev_u [2][ny][nx] (u_x then u_y, Eq. (25b)), dev_p [ny][nx] (Eq. (25c)).
+ * Any pointer may be NULL.  Asynchronous. */
+nlbm_status nlbm_get_moments(nlbm_sim *s, float *dev_phi, float *dev_u, float *dev_p);
+
+/* As nlbm_get_moments() into host memory; synchronizes. */
+nlbm_status nlbm_get_moments_host(nlbm_sim *s, float *host_phi, float *host_u, float *host_p);
+
+/* Per-phase volume sum_x phi_p of the most recent step's phase fields,
+ * accumulated in FP64 with a fixed reduction order (bitwise reproducible),
+ * into host_mass [N].  Returns EDIVERGED (masses still written) when any
+ * phi_p is non-finite or outside [-0.5, 1.5].  Synchronizes. */
+nlbm_status nlbm_phase_mass(nlbm_sim *s, double *host_mass);
+
+/* Bytes of a checkpoint of the full state (populations, auxiliary fields,
+ * last moments).  Host only. */
+nlbm_status nlbm_state_bytes(const nlbm_sim *s, size_t *bytes);
+
+/* Copy the full state (populations, auxiliary fields, last moments and the
+ * step counter) into / from caller device memory of nlbm_state_bytes()
+ * bytes, 16-byte aligned.  Both synchronize (the step counter travels
+ * through host memory).  Restore returns EINVAL if the buffer does not carry
+ * the checkpoint tag written by nlbm_save(). */
+nlbm_status nlbm_save(nlbm_sim *s, void *dev_dst);
+nlbm_status nlbm_restore(nlbm_sim *s, const void *dev_src);
+
+/* Wait for all work enqueued by this simulation.  Synchronizes. */
+nlbm_status nlbm_synchronize(nlbm_sim *s);
+
+/* Steps taken since nlbm_set_phi() (or the restored checkpoint). */
+int64_t nlbm_steps_done(const nlbm_sim *s);
+
+/* Number of kernels this handle has launched since creation. */
+int64_t nlbm_kernel_launches(const nlbm_sim *s);
+
+/* Tile of the fused step kernel: tx columns per thread block (one thread
+ * per column; 32..256, a multiple of 32) marching down ty rows (>= 1).
+ * EINVAL outside those ranges.  Takes effect on the next nlbm_step(). */
+nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
+nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
+
+/* Release the handle (not the workspace).  Safe on NULL.  Does not wait for
+ * enqueued work; synchronize first if the workspace is to be reused. */
+void nlbm_destroy(nlbm_sim *s);
+
+/* Text of the last error of this handle ("" if none); s may be NULL for the
+ * last error of a failed nlbm_create / nlbm_workspace_bytes on this thread. */
+const char *nlbm_last_error(const nlbm_sim *s);
+
+/* Static text of a status code. */
+const char *nlbm_status_string(nlbm_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLBM_H */

@@ -2,4 +2,4 @@
 method (arXiv 2306.06983).  Test infrastructure only: imported by the tests,
 the smoke check and the benchmark's CPU-baseline leg, never by the library."""
 
-from .oracle import OracleSim, build_oracle, oracle_lib, params_struct  # noqa: F401
+from .oracle import OracleSim, build_oracle, oracle_lib, oracle_lib_fp32, params_struct  # noqa: F401

@@ -59,13 +59,30 @@
 #define Q 9
 #define MAXN 8
 
+/* Working precision.  The oracle is FP64 (the default).  Built with
+ * -DORACLE_FP32 the same source runs in FP32 as a noise model: the spread
+ * between the two builds is what FP32 rounding alone does to the method,
+ * which sets the scale of the GPU parity tolerances.  The FP32 build is
+ * never a reference value. */
+#ifdef ORACLE_FP32
+typedef float real;
+#define RSQRT_(x) sqrtf(x)
+#define RPOW_(x, y) powf(x, y)
+#define RFABS_(x) fabsf(x)
+#else
+typedef double real;
+#define RSQRT_(x) sqrt(x)
+#define RPOW_(x, y) pow(x, y)
+#define RFABS_(x) fabs(x)
+#endif
+
 /* D2Q9 lattice, Sec. 4: the velocity order is the column order of the
  * moment matrix in Eq. (28); c_s^2 = 1/3 with dx = dt = 1. */
 static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const double W[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+static const real W[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-static const double CS2 = 1.0 / 3.0;
+static const real CS2 = 1.0 / 3.0;
 
 typedef struct {
     int32_t nx, ny;
@@ -86,28 +103,28 @@ typedef struct {
     or_params p;
     int N, L;           /* phases, LB-solved phase sets */
     size_t n;           /* nodes */
-    double Mm[Q][Q], Mi[Q][Q];
-    double tau_f;
+    real Mm[Q][Q], Mi[Q][Q];
+    real tau_f;
     long long steps;
     /* state */
-    double *f, *fn;     /* [L][Q][n] post-streaming populations, spare */
-    double *g, *gn;     /* [Q][n] */
-    double *phi_prev;   /* [N][n] */
-    double *u_prev;     /* [2][n] */
-    double *mphi_prev;  /* [2][n] */
+    real *f, *fn;     /* [L][Q][n] post-streaming populations, spare */
+    real *g, *gn;     /* [Q][n] */
+    real *phi_prev;   /* [N][n] */
+    real *u_prev;     /* [2][n] */
+    real *mphi_prev;  /* [2][n] */
     /* last computed macroscopic fields */
-    double *phi;        /* [N][n] */
-    double *u;          /* [2][n] */
-    double *P;          /* [n] */
+    real *phi;        /* [N][n] */
+    real *u;          /* [2][n] */
+    real *P;          /* [n] */
     /* per-step work fields */
-    double *grad;       /* [N][2][n] */
-    double *lap;        /* [N][n] */
-    double *R;          /* [N][2][n] */
-    double *mphi;       /* [2][n] */
-    double *muphi;      /* [N][n] */
-    double *F;          /* [2][n] total force */
-    double *rho, *mu;   /* [n] */
-    double *gradrho;    /* [2][n] */
+    real *grad;       /* [N][2][n] */
+    real *lap;        /* [N][n] */
+    real *R;          /* [N][2][n] */
+    real *mphi;       /* [2][n] */
+    real *muphi;      /* [N][n] */
+    real *F;          /* [2][n] total force */
+    real *rho, *mu;   /* [n] */
+    real *gradrho;    /* [2][n] */
 } or_sim;
 
 /* ---------------------------------------------------------------- helpers */
@@ -136,7 +153,7 @@ static size_t nid(const or_sim *s, int x, int y) { return (size_t)y * s->p.nx + 
  * (its component normal to the mirrored wall is negated). */
 enum { K_SCALAR = 0, K_VELOCITY = 1, K_REFLECT = 2 };
 
-static double fetch_scalar(const or_sim *s, const double *F, int x, int y)
+static real fetch_scalar(const or_sim *s, const real *F, int x, int y)
 {
     int fx, fy;
     int xx = map_coord(x, s->p.nx, s->p.wall_x, &fx);
@@ -144,14 +161,14 @@ static double fetch_scalar(const or_sim *s, const double *F, int x, int y)
     return F[nid(s, xx, yy)];
 }
 
-static void fetch_vec(const or_sim *s, const double *V, int x, int y, int kind,
-                      double *vx, double *vy)
+static void fetch_vec(const or_sim *s, const real *V, int x, int y, int kind,
+                      real *vx, real *vy)
 {
     int fx, fy;
     int xx = map_coord(x, s->p.nx, s->p.wall_x, &fx);
     int yy = map_coord(y, s->p.ny, s->p.wall_y, &fy);
     size_t k = nid(s, xx, yy);
-    double a = V[k], b = V[s->n + k];
+    real a = V[k], b = V[s->n + k];
     if (kind == K_VELOCITY) {
         if (fx) { a = -a; b = -b; }
         if (fy) { a = -a; b = -b; }
@@ -164,11 +181,11 @@ static void fetch_vec(const or_sim *s, const double *V, int x, int y, int kind,
 }
 
 /* Sec. 3, Eq. (27): grad chi = sum_{i!=0} w_i c_i chi(x+c_i) / (c_s^2 dt). */
-static void grad_at(const or_sim *s, const double *F, int x, int y, double *gx, double *gy)
+static void grad_at(const or_sim *s, const real *F, int x, int y, real *gx, real *gy)
 {
-    double ax = 0, ay = 0;
+    real ax = 0, ay = 0;
     for (int i = 1; i < Q; i++) {
-        double v = fetch_scalar(s, F, x + CX[i], y + CY[i]);
+        real v = fetch_scalar(s, F, x + CX[i], y + CY[i]);
         ax += W[i] * CX[i] * v;
         ay += W[i] * CY[i] * v;
     }
@@ -177,19 +194,19 @@ static void grad_at(const or_sim *s, const double *F, int x, int y, double *gx, 
 }
 
 /* Sec. 3, Eq. (27): lap chi = sum_{i!=0} 2 w_i (chi(x+c_i) - chi(x)) / (c_s^2 dt^2). */
-static double lap_at(const or_sim *s, const double *F, int x, int y)
+static real lap_at(const or_sim *s, const real *F, int x, int y)
 {
-    double c0 = fetch_scalar(s, F, x, y), a = 0;
+    real c0 = fetch_scalar(s, F, x, y), a = 0;
     for (int i = 1; i < Q; i++) a += 2.0 * W[i] * (fetch_scalar(s, F, x + CX[i], y + CY[i]) - c0);
     return a / CS2;
 }
 
 /* Unit vector with the zero-gradient reading: 0 when |v|^2 <= 1e-24. */
-static void unit(double vx, double vy, double *nx, double *ny)
+static void unit(real vx, real vy, real *nx, real *ny)
 {
-    double n2 = vx * vx + vy * vy;
+    real n2 = vx * vx + vy * vy;
     if (n2 > 1e-24) {
-        double r = sqrt(n2);
+        real r = RSQRT_(n2);
         *nx = vx / r;
         *ny = vy / r;
     } else {
@@ -199,27 +216,27 @@ static void unit(double vx, double vy, double *nx, double *ny)
 }
 
 /* Invert a 9x9 matrix by Gauss-Jordan elimination with partial pivoting. */
-static int invert9(double A[Q][Q], double B[Q][Q])
+static int invert9(real A[Q][Q], real B[Q][Q])
 {
-    double T[Q][2 * Q];
+    real T[Q][2 * Q];
     for (int i = 0; i < Q; i++)
         for (int j = 0; j < 2 * Q; j++) T[i][j] = j < Q ? A[i][j] : (j - Q == i);
     for (int c = 0; c < Q; c++) {
         int piv = c;
         for (int r = c + 1; r < Q; r++)
-            if (fabs(T[r][c]) > fabs(T[piv][c])) piv = r;
-        if (fabs(T[piv][c]) < 1e-14) return -1;
+            if (RFABS_(T[r][c]) > RFABS_(T[piv][c])) piv = r;
+        if (RFABS_(T[piv][c]) < (real)1e-7) return -1;
         if (piv != c)
             for (int j = 0; j < 2 * Q; j++) {
-                double t = T[c][j];
+                real t = T[c][j];
                 T[c][j] = T[piv][j];
                 T[piv][j] = t;
             }
-        double d = T[c][c];
+        real d = T[c][c];
         for (int j = 0; j < 2 * Q; j++) T[c][j] /= d;
         for (int r = 0; r < Q; r++)
             if (r != c) {
-                double f = T[r][c];
+                real f = T[r][c];
                 if (f != 0)
                     for (int j = 0; j < 2 * Q; j++) T[r][j] -= f * T[c][j];
             }
@@ -231,10 +248,10 @@ static int invert9(double A[Q][Q], double B[Q][Q])
 
 /* Sec. 4, Eq. (28): rows 1, c_x, c_y, c_x^2, c_y^2, c_x c_y, c_x^2 c_y,
  * c_x c_y^2, c_x^2 c_y^2 evaluated on the velocity set. */
-static void build_M(double Mm[Q][Q])
+static void build_M(real Mm[Q][Q])
 {
     for (int i = 0; i < Q; i++) {
-        double x = CX[i], y = CY[i];
+        real x = CX[i], y = CY[i];
         Mm[0][i] = 1;
         Mm[1][i] = x;
         Mm[2][i] = y;
@@ -248,12 +265,12 @@ static void build_M(double Mm[Q][Q])
 }
 
 /* Moment-space MRT update, Sec. 4: out = f - M^-1 S M (f - feq) + M^-1 (I - S/2) M src. */
-static void mrt(const or_sim *s, const double f[Q], const double feq[Q], const double src[Q],
-                const double S[Q], double out[Q])
+static void mrt(const or_sim *s, const real f[Q], const real feq[Q], const real src[Q],
+                const real S[Q], real out[Q])
 {
-    double m[Q], meq[Q], ms[Q], mstar[Q];
+    real m[Q], meq[Q], ms[Q], mstar[Q];
     for (int k = 0; k < Q; k++) {
-        double a = 0, b = 0, c = 0;
+        real a = 0, b = 0, c = 0;
         for (int i = 0; i < Q; i++) {
             a += s->Mm[k][i] * f[i];
             b += s->Mm[k][i] * feq[i];
@@ -265,7 +282,7 @@ static void mrt(const or_sim *s, const double f[Q], const double feq[Q], const d
     }
     for (int k = 0; k < Q; k++) mstar[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * ms[k];
     for (int i = 0; i < Q; i++) {
-        double a = 0;
+        real a = 0;
         for (int k = 0; k < Q; k++) a += s->Mi[i][k] * mstar[k];
         out[i] = a;
     }
@@ -274,13 +291,13 @@ static void mrt(const or_sim *s, const double f[Q], const double feq[Q], const d
 /* ------------------------------------------------- pointwise model pieces */
 
 /* Sec. 3, Eq. (19): f^eq_i = w_i phi (1 + c_i.u / c_s^2). */
-void or_phase_feq(double phi, double ux, double uy, double out[Q])
+void or_phase_feq(real phi, real ux, real uy, real out[Q])
 {
     for (int i = 0; i < Q; i++) out[i] = W[i] * phi * (1.0 + (CX[i] * ux + CY[i] * uy) / CS2);
 }
 
 /* Sec. 3, Eq. (19): R_i = w_i [c_i . d_t(phi u) / c_s^2 + c_i . R_p]. */
-void or_phase_src(double dtphiux, double dtphiuy, double Rx, double Ry, double out[Q])
+void or_phase_src(real dtphiux, real dtphiuy, real Rx, real Ry, real out[Q])
 {
     for (int i = 0; i < Q; i++)
         out[i] = W[i] * ((CX[i] * dtphiux + CY[i] * dtphiuy) / CS2 + CX[i] * Rx + CY[i] * Ry);
@@ -289,15 +306,15 @@ void or_phase_src(double dtphiux, double dtphiuy, double Rx, double Ry, double o
 /* Sec. 3, Eq. (22): g^eq_i = lambda_i + w_i [c_i.(rho u)/c_s^2
  *   + (m u):(c_i c_i - c_s^2 I)/(2 c_s^4)], lambda_0 = (w_0 - 1) P/c_s^2 + rho_0,
  *   lambda_i = w_i P / c_s^2. */
-void or_flow_geq(double P, double rho0, double rho, double ux, double uy, double mx, double my,
-                 double out[Q])
+void or_flow_geq(real P, real rho0, real rho, real ux, real uy, real mx, real my,
+                 real out[Q])
 {
     for (int i = 0; i < Q; i++) {
-        double lam = i == 0 ? (W[0] - 1.0) * P / CS2 + rho0 : W[i] * P / CS2;
-        double cu = CX[i] * ux + CY[i] * uy;
-        double cm = CX[i] * mx + CY[i] * my;
+        real lam = i == 0 ? (W[0] - 1.0) * P / CS2 + rho0 : W[i] * P / CS2;
+        real cu = CX[i] * ux + CY[i] * uy;
+        real cm = CX[i] * mx + CY[i] * my;
         /* (m u):(c c - c_s^2 I) = (m.c)(u.c) - c_s^2 m.u */
-        double mu2 = cm * cu - CS2 * (mx * ux + my * uy);
+        real mu2 = cm * cu - CS2 * (mx * ux + my * uy);
         out[i] = lam + W[i] * (rho * cu / CS2 + mu2 / (2.0 * CS2 * CS2));
     }
 }
@@ -305,12 +322,12 @@ void or_flow_geq(double P, double rho0, double rho, double ux, double uy, double
 /* Sec. 3, Eq. (23): F_i = w_i [u.grad rho + c_i.F/c_s^2
  *   + (M_2F - c_s^2 (u.grad rho) I):(c_i c_i - c_s^2 I)/(2 c_s^4)],
  * with M_2F given as its components (xx, xy, yx, yy). */
-void or_flow_force(double ugr, double Fx, double Fy, const double M2F[4], double out[Q])
+void or_flow_force(real ugr, real Fx, real Fy, const real M2F[4], real out[Q])
 {
     for (int i = 0; i < Q; i++) {
-        double T[2][2] = {{M2F[0] - CS2 * ugr, M2F[1]}, {M2F[2], M2F[3] - CS2 * ugr}};
-        double c[2] = {(double)CX[i], (double)CY[i]};
-        double con = 0;
+        real T[2][2] = {{M2F[0] - CS2 * ugr, M2F[1]}, {M2F[2], M2F[3] - CS2 * ugr}};
+        real c[2] = {(real)CX[i], (real)CY[i]};
+        real con = 0;
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) con += T[a][b] * (c[a] * c[b] - (a == b ? CS2 : 0.0));
         out[i] = W[i] * (ugr + (c[0] * Fx + c[1] * Fy) / CS2 + con / (2.0 * CS2 * CS2));
@@ -318,28 +335,28 @@ void or_flow_force(double ugr, double Fx, double Fy, const double M2F[4], double
 }
 
 /* g'(s) for g(s) = s^2 (1-s)^2, Sec. 2.2 below Eq. (14). */
-static double gprime(double s) { return 2.0 * s * (1.0 - s) * (1.0 - 2.0 * s); }
+static real gprime(real s) { return 2.0 * s * (1.0 - s) * (1.0 - 2.0 * s); }
 
 /* Sec. 2.1, Eqs. (2)-(4): source R_p at one node for all N phases, given
  * phi[N] and grad phi[N][2]. */
-static void source_at(const or_params *pp, int N, const double *phi, const double (*gp)[2],
-                      double (*R)[2])
+static void source_at(const or_params *pp, int N, const real *phi, const real (*gp)[2],
+                      real (*R)[2])
 {
-    const double eps = pp->eps;
+    const real eps = pp->eps;
     if (pp->model == 0) {
         /* Model A, Eq. (2): R_p = a_p n_p - beta_p,
          * beta_p = phi_p^n / sum_q phi_q^n * sum_q a_q n_q, a_q = 4 phi_q (1-phi_q)/eps */
-        double sumw = 0, Vx = 0, Vy = 0, a[MAXN], nvx[MAXN], nvy[MAXN], w[MAXN];
+        real sumw = 0, Vx = 0, Vy = 0, a[MAXN], nvx[MAXN], nvy[MAXN], w[MAXN];
         for (int q = 0; q < N; q++) {
             a[q] = 4.0 * phi[q] * (1.0 - phi[q]) / eps;
             unit(gp[q][0], gp[q][1], &nvx[q], &nvy[q]);
-            w[q] = pow(phi[q] > 0 ? phi[q] : 0.0, pp->model_a_n);
+            w[q] = RPOW_(phi[q] > 0 ? phi[q] : (real)0, (real)pp->model_a_n);
             sumw += w[q];
             Vx += a[q] * nvx[q];
             Vy += a[q] * nvy[q];
         }
         for (int p = 0; p < N; p++) {
-            double b = w[p] / sumw;
+            real b = w[p] / sumw;
             R[p][0] = a[p] * nvx[p] - b * Vx;
             R[p][1] = a[p] * nvy[p] - b * Vy;
         }
@@ -347,14 +364,14 @@ static void source_at(const or_params *pp, int N, const double *phi, const doubl
         /* Model B, Eqs. (3)-(4): R_p = sum_{q!=p} 4 phi_p phi_q / eps n_pq,
          * n_pq = grad phi_pq / |grad phi_pq|, phi_pq = phi_p/(phi_p+phi_q). */
         for (int p = 0; p < N; p++) {
-            double rx = 0, ry = 0;
+            real rx = 0, ry = 0;
             for (int q = 0; q < N; q++) {
                 if (q == p) continue;
-                double vx = phi[q] * gp[p][0] - phi[p] * gp[q][0];
-                double vy = phi[q] * gp[p][1] - phi[p] * gp[q][1];
-                double ux, uy;
+                real vx = phi[q] * gp[p][0] - phi[p] * gp[q][0];
+                real vy = phi[q] * gp[p][1] - phi[p] * gp[q][1];
+                real ux, uy;
                 unit(vx, vy, &ux, &uy);
-                double c = 4.0 * phi[p] * phi[q] / eps;
+                real c = 4.0 * phi[p] * phi[q] / eps;
                 rx += c * ux;
                 ry += c * uy;
             }
@@ -388,7 +405,7 @@ void or_destroy(void *h)
 {
     or_sim *s = (or_sim *)h;
     if (!s) return;
-    double *bufs[] = {s->f, s->fn, s->g, s->gn, s->phi_prev, s->u_prev, s->mphi_prev, s->phi,
+    real *bufs[] = {s->f, s->fn, s->g, s->gn, s->phi_prev, s->u_prev, s->mphi_prev, s->phi,
                       s->u, s->P, s->grad, s->lap, s->R, s->mphi, s->muphi, s->F, s->rho, s->mu,
                       s->gradrho};
     for (size_t i = 0; i < sizeof bufs / sizeof bufs[0]; i++) free(bufs[i]);
@@ -414,7 +431,7 @@ void *or_create(const or_params *p)
     size_t n = s->n, N = s->N, L = s->L;
 #define ALLOC(ptr, cnt)                                  \
     do {                                                 \
-        (ptr) = (double *)calloc((cnt), sizeof(double)); \
+        (ptr) = (real *)calloc((cnt), sizeof(real)); \
         if (!(ptr)) {                                    \
             or_destroy(s);                               \
             return NULL;                                 \
@@ -446,13 +463,13 @@ void *or_create(const or_params *p)
 /* Initial state (reading: fluid at rest): phi given for phases 1..N-1,
  * phi_N = 1 - sum; f_i = w_i phi_p; g_i = lambda_i with P = 0 and rho_0 = 0,
  * i.e. g = 0; u = 0, P = 0; the "previous" fields equal the initial ones. */
-void or_set_phi(void *h, const double *phi_in)
+void or_set_phi(void *h, const real *phi_in)
 {
     or_sim *s = (or_sim *)h;
     size_t n = s->n;
     int N = s->N;
     for (size_t k = 0; k < n; k++) {
-        double sum = 0;
+        real sum = 0;
         for (int p = 0; p < N - 1; p++) {
             s->phi[p * n + k] = phi_in[p * n + k];
             sum += phi_in[p * n + k];
@@ -462,12 +479,12 @@ void or_set_phi(void *h, const double *phi_in)
     for (int p = 0; p < s->L; p++)
         for (int i = 0; i < Q; i++)
             for (size_t k = 0; k < n; k++) s->f[(p * Q + i) * n + k] = W[i] * s->phi[p * n + k];
-    memset(s->g, 0, Q * n * sizeof(double));
-    memcpy(s->phi_prev, s->phi, N * n * sizeof(double));
-    memset(s->u_prev, 0, 2 * n * sizeof(double));
-    memset(s->mphi_prev, 0, 2 * n * sizeof(double));
-    memset(s->u, 0, 2 * n * sizeof(double));
-    memset(s->P, 0, n * sizeof(double));
+    memset(s->g, 0, Q * n * sizeof(real));
+    memcpy(s->phi_prev, s->phi, N * n * sizeof(real));
+    memset(s->u_prev, 0, 2 * n * sizeof(real));
+    memset(s->mphi_prev, 0, 2 * n * sizeof(real));
+    memset(s->u, 0, 2 * n * sizeof(real));
+    memset(s->P, 0, n * sizeof(real));
     s->steps = 0;
 }
 
@@ -483,16 +500,16 @@ static void step_once(or_sim *s)
      * unless every phase is solved. */
 #pragma omp parallel for schedule(static)
     for (long long k = 0; k < (long long)n; k++) {
-        double sum = 0;
+        real sum = 0;
         for (int p = 0; p < L; p++) {
-            double a = 0;
+            real a = 0;
             for (int i = 0; i < Q; i++) a += s->f[(p * Q + i) * n + k];
             s->phi[p * n + k] = a;
             sum += a;
         }
         if (L == N - 1) s->phi[(N - 1) * n + k] = 1.0 - sum;
         /* Sec. 2.2, Eqs. (11),(12) */
-        double r = 0, m = 0;
+        real r = 0, m = 0;
         for (int p = 0; p < N; p++) {
             r += pp->rho[p] * s->phi[p * n + k];
             m += pp->mu[p] * s->phi[p * n + k];
@@ -507,13 +524,13 @@ static void step_once(or_sim *s)
         for (int x = 0; x < nx; x++) {
             size_t k = nid(s, x, y);
             for (int p = 0; p < N; p++) {
-                double gx, gy;
+                real gx, gy;
                 grad_at(s, s->phi + p * n, x, y, &gx, &gy);
                 s->grad[(p * 2 + 0) * n + k] = gx;
                 s->grad[(p * 2 + 1) * n + k] = gy;
                 s->lap[p * n + k] = lap_at(s, s->phi + p * n, x, y);
             }
-            double gx, gy;
+            real gx, gy;
             grad_at(s, s->rho, x, y, &gx, &gy);
             s->gradrho[k] = gx;
             s->gradrho[n + k] = gy;
@@ -523,14 +540,14 @@ static void step_once(or_sim *s)
      * Sec. 2.2, Eqs. (15)-(17): chemical potentials; Eq. (16): F_s. */
 #pragma omp parallel for schedule(static)
     for (long long k = 0; k < (long long)n; k++) {
-        double ph[MAXN], gp[MAXN][2], R[MAXN][2];
+        real ph[MAXN], gp[MAXN][2], R[MAXN][2];
         for (int p = 0; p < N; p++) {
             ph[p] = s->phi[p * n + k];
             gp[p][0] = s->grad[(p * 2 + 0) * n + k];
             gp[p][1] = s->grad[(p * 2 + 1) * n + k];
         }
-        source_at(pp, N, ph, (const double(*)[2])gp, R);
-        double mx = 0, my = 0;
+        source_at(pp, N, ph, (const real(*)[2])gp, R);
+        real mx = 0, my = 0;
         for (int p = 0; p < N; p++) {
             s->R[(p * 2 + 0) * n + k] = R[p][0];
             s->R[(p * 2 + 1) * n + k] = R[p][1];
@@ -539,14 +556,14 @@ static void step_once(or_sim *s)
         }
         s->mphi[k] = mx;
         s->mphi[n + k] = my;
-        double fsx = 0, fsy = 0;
+        real fsx = 0, fsy = 0;
         for (int p = 0; p < N; p++) {
-            double mu = 0;
+            real mu = 0;
             for (int q = 0; q < N; q++) {
                 if (q == p) continue;
-                double sig = pp->sigma[p * MAXN + q];
-                double beta = 3.0 * sig / pp->eps;           /* Eq. (15) */
-                double kpq = -3.0 * pp->eps * sig / 4.0;      /* Eq. (15) */
+                real sig = pp->sigma[p * MAXN + q];
+                real beta = 3.0 * sig / pp->eps;           /* Eq. (15) */
+                real kpq = -3.0 * pp->eps * sig / 4.0;      /* Eq. (15) */
                 mu += 2.0 * beta * (gprime(ph[p]) - gprime(ph[p] + ph[q]));
                 mu -= kpq * s->lap[q * n + k];
             }
@@ -564,12 +581,12 @@ static void step_once(or_sim *s)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t k = nid(s, x, y);
-            double div[2] = {0, 0};
+            real div[2] = {0, 0};
             for (int i = 1; i < Q; i++) {
-                double mx, my, ux, uy;
+                real mx, my, ux, uy;
                 fetch_vec(s, s->mphi, x + CX[i], y + CY[i], K_REFLECT, &mx, &my);
                 fetch_vec(s, s->u_prev, x + CX[i], y + CY[i], K_VELOCITY, &ux, &uy);
-                double m[2] = {mx, my}, u[2] = {ux, uy}, c[2] = {(double)CX[i], (double)CY[i]};
+                real m[2] = {mx, my}, u[2] = {ux, uy}, c[2] = {(real)CX[i], (real)CY[i]};
                 for (int b = 0; b < 2; b++)
                     for (int a = 0; a < 2; a++)
                         div[b] += W[i] * c[a] * (m[a] * u[b] - u[a] * m[b]) / CS2;
@@ -580,35 +597,35 @@ static void step_once(or_sim *s)
 
     /* Macroscopic velocity and pressure, Eqs. (25b),(25c); collisions,
      * Eqs. (18)-(24); then streaming. */
-    const double Sph[Q] = {1, 1.0 / s->tau_f, 1.0 / s->tau_f, 1, 1, 1, 1, 1, 1};
+    const real Sph[Q] = {1, 1.0 / s->tau_f, 1.0 / s->tau_f, 1, 1, 1, 1, 1, 1};
 #pragma omp parallel for schedule(static)
     for (long long k = 0; k < (long long)n; k++) {
-        double gk[Q];
+        real gk[Q];
         for (int i = 0; i < Q; i++) gk[i] = s->g[i * n + k];
-        double Fx = s->F[k], Fy = s->F[n + k];
-        double rho = s->rho[k];
-        double jx = 0, jy = 0, sg = 0;
+        real Fx = s->F[k], Fy = s->F[n + k];
+        real rho = s->rho[k];
+        real jx = 0, jy = 0, sg = 0;
         for (int i = 0; i < Q; i++) {
             jx += CX[i] * gk[i];
             jy += CY[i] * gk[i];
             if (i) sg += gk[i];
         }
         /* Eq. (25b): rho u = sum c_i g_i + dt F / 2 */
-        double ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;
-        double mphx = s->mphi[k], mphy = s->mphi[n + k];
+        real ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;
+        real mphx = s->mphi[k], mphy = s->mphi[n + k];
         /* Eq. (13): m = rho u + m_phi */
-        double mx = rho * ux + mphx, my = rho * uy + mphy;
-        double grx = s->gradrho[k], gry = s->gradrho[n + k];
-        double ugr = ux * grx + uy * gry;
+        real mx = rho * ux + mphx, my = rho * uy + mphy;
+        real grx = s->gradrho[k], gry = s->gradrho[n + k];
+        real ugr = ux * grx + uy * gry;
         /* previous-step quantities for backward Euler */
-        double upx = s->u_prev[k], upy = s->u_prev[n + k];
-        double rho_p = 0;
+        real upx = s->u_prev[k], upy = s->u_prev[n + k];
+        real rho_p = 0;
         for (int p = 0; p < N; p++) rho_p += pp->rho[p] * s->phi_prev[p * n + k];
-        double mpx = rho_p * upx + s->mphi_prev[k], mpy = rho_p * upy + s->mphi_prev[n + k];
-        double mu_t = (mx * ux + my * uy), mu_prev = (mpx * upx + mpy * upy);
-        double dt_mu = mu_t - mu_prev;
+        real mpx = rho_p * upx + s->mphi_prev[k], mpy = rho_p * upy + s->mphi_prev[n + k];
+        real mu_t = (mx * ux + my * uy), mu_prev = (mpx * upx + mpy * upy);
+        real dt_mu = mu_t - mu_prev;
         /* Eq. (25c) */
-        double P = CS2 / (1.0 - W[0]) *
+        real P = CS2 / (1.0 - W[0]) *
                    (sg + 0.5 * ugr - W[0] * mu_t / (2.0 * CS2) + W[0] * 0.5 * dt_mu / (2.0 * CS2));
         s->u[k] = ux;
         s->u[n + k] = uy;
@@ -616,30 +633,30 @@ static void step_once(or_sim *s)
 
         /* Phase-field collision per solved phase, Eqs. (18),(19). */
         for (int p = 0; p < L; p++) {
-            double fk[Q], feq[Q], src[Q], out[Q];
+            real fk[Q], feq[Q], src[Q], out[Q];
             for (int i = 0; i < Q; i++) fk[i] = s->f[(p * Q + i) * n + k];
-            double ph = s->phi[p * n + k], php = s->phi_prev[p * n + k];
+            real ph = s->phi[p * n + k], php = s->phi_prev[p * n + k];
             or_phase_feq(ph, ux, uy, feq);
-            double dtx = ph * ux - php * upx, dty = ph * uy - php * upy;
+            real dtx = ph * ux - php * upx, dty = ph * uy - php * upy;
             or_phase_src(dtx, dty, s->R[(p * 2 + 0) * n + k], s->R[(p * 2 + 1) * n + k], src);
             mrt(s, fk, feq, src, Sph, out);
             for (int i = 0; i < Q; i++) s->f[(p * Q + i) * n + k] = out[i]; /* post-collision */
         }
 
         /* Flow collision, Eqs. (21)-(24), tau_g from Eq. (26). */
-        double tau_g = s->mu[k] / (rho * CS2) + 0.5;
-        double s2 = 1.0 / tau_g;
-        const double Sfl[Q] = {1, 1, 1, s2, s2, s2, 1, 1, 1};
-        double geq[Q], Fi[Q], out[Q];
+        real tau_g = s->mu[k] / (rho * CS2) + 0.5;
+        real s2 = 1.0 / tau_g;
+        const real Sfl[Q] = {1, 1, 1, s2, s2, s2, 1, 1, 1};
+        real geq[Q], Fi[Q], out[Q];
         or_flow_geq(P, 0.0, rho, ux, uy, mx, my, geq);
         /* M_2F = d_t(rho u u) + d_t((m_phi u + u m_phi)/2) + c_s^2 (u grad rho + grad rho u)
          *        + c_s^2 (u.grad rho) I, with d_t(rho u u) ~ u F + F u. */
-        double u[2] = {ux, uy}, Fv[2] = {Fx, Fy}, gr[2] = {grx, gry};
-        double mp[2] = {mphx, mphy}, mpp[2] = {s->mphi_prev[k], s->mphi_prev[n + k]}, up[2] = {upx, upy};
-        double M2F[4];
+        real u[2] = {ux, uy}, Fv[2] = {Fx, Fy}, gr[2] = {grx, gry};
+        real mp[2] = {mphx, mphy}, mpp[2] = {s->mphi_prev[k], s->mphi_prev[n + k]}, up[2] = {upx, upy};
+        real M2F[4];
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) {
-                double v = u[a] * Fv[b] + Fv[a] * u[b];
+                real v = u[a] * Fv[b] + Fv[a] * u[b];
                 v += 0.5 * (mp[a] * u[b] + u[a] * mp[b]) - 0.5 * (mpp[a] * up[b] + up[a] * mpp[b]);
                 v += CS2 * (u[a] * gr[b] + gr[a] * u[b]);
                 if (a == b) v += CS2 * ugr;
@@ -676,7 +693,7 @@ static void step_once(or_sim *s)
                 s->gn[di * n + dst] = s->g[i * n + k];
             }
         }
-    double *t = s->f;
+    real *t = s->f;
     s->f = s->fn;
     s->fn = t;
     t = s->g;
@@ -684,9 +701,9 @@ static void step_once(or_sim *s)
     s->gn = t;
 
     /* Store the "previous" fields for the next step's time derivatives. */
-    memcpy(s->phi_prev, s->phi, N * n * sizeof(double));
-    memcpy(s->u_prev, s->u, 2 * n * sizeof(double));
-    memcpy(s->mphi_prev, s->mphi, 2 * n * sizeof(double));
+    memcpy(s->phi_prev, s->phi, N * n * sizeof(real));
+    memcpy(s->u_prev, s->u, 2 * n * sizeof(real));
+    memcpy(s->mphi_prev, s->mphi, 2 * n * sizeof(real));
     s->steps++;
 }
 
@@ -702,20 +719,20 @@ void or_step(void *h, long long nsteps, int nthreads)
 
 /* Last computed macroscopic fields: phi [N][ny][nx], u [2][ny][nx], P [ny][nx].
  * Any pointer may be NULL. */
-void or_get_moments(void *h, double *phi, double *u, double *P)
+void or_get_moments(void *h, real *phi, real *u, real *P)
 {
     or_sim *s = (or_sim *)h;
-    if (phi) memcpy(phi, s->phi, s->N * s->n * sizeof(double));
-    if (u) memcpy(u, s->u, 2 * s->n * sizeof(double));
-    if (P) memcpy(P, s->P, s->n * sizeof(double));
+    if (phi) memcpy(phi, s->phi, s->N * s->n * sizeof(real));
+    if (u) memcpy(u, s->u, 2 * s->n * sizeof(real));
+    if (P) memcpy(P, s->P, s->n * sizeof(real));
 }
 
 /* Per-phase mass sum_x phi_p of the last computed fields, p = 1..N. */
-void or_phase_mass(void *h, double *mass)
+void or_phase_mass(void *h, real *mass)
 {
     or_sim *s = (or_sim *)h;
     for (int p = 0; p < s->N; p++) {
-        double a = 0;
+        real a = 0;
         for (size_t k = 0; k < s->n; k++) a += s->phi[p * s->n + k];
         mass[p] = a;
     }
@@ -724,17 +741,17 @@ void or_phase_mass(void *h, double *mass)
 /* Intermediate fields of the last step (for inspection in tests):
  * which = 0 R [N][2][n], 1 m_phi [2][n], 2 mu_phi [N][n], 3 F [2][n],
  *         4 grad phi [N][2][n], 5 lap phi [N][n]. */
-void or_get_field(void *h, int which, double *out)
+void or_get_field(void *h, int which, real *out)
 {
     or_sim *s = (or_sim *)h;
     size_t n = s->n, N = s->N;
     switch (which) {
-    case 0: memcpy(out, s->R, N * 2 * n * sizeof(double)); break;
-    case 1: memcpy(out, s->mphi, 2 * n * sizeof(double)); break;
-    case 2: memcpy(out, s->muphi, N * n * sizeof(double)); break;
-    case 3: memcpy(out, s->F, 2 * n * sizeof(double)); break;
-    case 4: memcpy(out, s->grad, N * 2 * n * sizeof(double)); break;
-    case 5: memcpy(out, s->lap, N * n * sizeof(double)); break;
+    case 0: memcpy(out, s->R, N * 2 * n * sizeof(real)); break;
+    case 1: memcpy(out, s->mphi, 2 * n * sizeof(real)); break;
+    case 2: memcpy(out, s->muphi, N * n * sizeof(real)); break;
+    case 3: memcpy(out, s->F, 2 * n * sizeof(real)); break;
+    case 4: memcpy(out, s->grad, N * 2 * n * sizeof(real)); break;
+    case 5: memcpy(out, s->lap, N * n * sizeof(real)); break;
     default: break;
     }
 }
@@ -745,7 +762,7 @@ long long or_steps_done(void *h) { return ((or_sim *)h)->steps; }
 
 /* Eq. (27) applied to a standalone scalar field with the oracle's ghost
  * rules: grad -> out[2][ny][nx], lap -> out[ny][nx]. */
-void or_field_grad(const double *chi, int nx, int ny, int wall_x, int wall_y, double *out)
+void or_field_grad(const real *chi, int nx, int ny, int wall_x, int wall_y, real *out)
 {
     or_sim tmp;
     memset(&tmp, 0, sizeof tmp);
@@ -756,14 +773,14 @@ void or_field_grad(const double *chi, int nx, int ny, int wall_x, int wall_y, do
     tmp.n = (size_t)nx * ny;
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
-            double gx, gy;
+            real gx, gy;
             grad_at(&tmp, chi, x, y, &gx, &gy);
             out[nid(&tmp, x, y)] = gx;
             out[tmp.n + nid(&tmp, x, y)] = gy;
         }
 }
 
-void or_field_lap(const double *chi, int nx, int ny, int wall_x, int wall_y, double *out)
+void or_field_lap(const real *chi, int nx, int ny, int wall_x, int wall_y, real *out)
 {
     or_sim tmp;
     memset(&tmp, 0, sizeof tmp);
@@ -777,23 +794,23 @@ void or_field_lap(const double *chi, int nx, int ny, int wall_x, int wall_y, dou
 }
 
 /* Pointwise source of Eqs. (2)-(4) for all N phases: phi[N], grad[N][2] -> R[N][2]. */
-int or_point_source(const or_params *p, const double *phi, const double *grad, double *R)
+int or_point_source(const or_params *p, const real *phi, const real *grad, real *R)
 {
     if (p->n_phases < 2 || p->n_phases > MAXN) return -1;
-    source_at(p, p->n_phases, phi, (const double(*)[2])grad, (double(*)[2])R);
+    source_at(p, p->n_phases, phi, (const real(*)[2])grad, (real(*)[2])R);
     return 0;
 }
 
 /* Pointwise chemical potentials of Eq. (17): phi[N], lap[N] -> muphi[N]. */
-int or_point_chempot(const or_params *p, const double *phi, const double *lap, double *muphi)
+int or_point_chempot(const or_params *p, const real *phi, const real *lap, real *muphi)
 {
     int N = p->n_phases;
     if (N < 2 || N > MAXN) return -1;
     for (int a = 0; a < N; a++) {
-        double mu = 0;
+        real mu = 0;
         for (int b = 0; b < N; b++) {
             if (b == a) continue;
-            double sig = p->sigma[a * MAXN + b];
+            real sig = p->sigma[a * MAXN + b];
             mu += 2.0 * (3.0 * sig / p->eps) * (gprime(phi[a]) - gprime(phi[a] + phi[b]));
             mu -= (-3.0 * p->eps * sig / 4.0) * lap[b];
         }
@@ -803,9 +820,9 @@ int or_point_chempot(const or_params *p, const double *phi, const double *lap, d
 }
 
 /* The moment matrix of Eq. (28) and its numerical inverse (row-major 9x9). */
-void or_mrt_matrices(double *Mout, double *Miout)
+void or_mrt_matrices(real *Mout, real *Miout)
 {
-    double Mm[Q][Q], Mi[Q][Q];
+    real Mm[Q][Q], Mi[Q][Q];
     build_M(Mm);
     invert9(Mm, Mi);
     memcpy(Mout, Mm, sizeof Mm);

@@ -22,10 +22,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nlbm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB32 = os.path.join(_BUILD, "liboracle_fp32.so")
 MAXN = 8
 
 _lock = threading.Lock()
 _lib = None
+_lib32 = None
 
 
 class params_struct(ctypes.Structure):
@@ -41,18 +43,50 @@ class params_struct(ctypes.Structure):
     ]
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile the oracle into a shared library (idempotent, mtime-checked)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-o", tmp, _SRC, "-lm"]
+def _compile(out: str, extra) -> None:
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           *extra, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    os.replace(tmp, out)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the FP64 oracle and its FP32 noise-model build (idempotent,
+    mtime-checked); returns the FP64 library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for out, extra in ((_LIB, []), (_LIB32, ["-DORACLE_FP32", "-fsingle-precision-constant"])):
+        if (force or not os.path.exists(out)
+                or os.path.getmtime(out) < os.path.getmtime(_SRC)):
+            _compile(out, extra)
     return _LIB
+
+
+def _declare_sim(lib, real):
+    P = ctypes.POINTER
+    lib.or_create.restype = ctypes.c_void_p
+    lib.or_create.argtypes = [P(params_struct)]
+    lib.or_destroy.argtypes = [ctypes.c_void_p]
+    lib.or_set_phi.argtypes = [ctypes.c_void_p, P(real)]
+    lib.or_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]
+    lib.or_get_moments.argtypes = [ctypes.c_void_p, P(real), P(real), P(real)]
+    lib.or_phase_mass.argtypes = [ctypes.c_void_p, P(real)]
+    lib.or_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, P(real)]
+    lib.or_steps_done.restype = ctypes.c_longlong
+    lib.or_steps_done.argtypes = [ctypes.c_void_p]
+    lib.or_max_threads.restype = ctypes.c_int
+
+
+def oracle_lib_fp32():
+    """The FP32 build of the same source: a noise model, never a reference."""
+    global _lib32
+    with _lock:
+        if _lib32 is None:
+            build_oracle()
+            lib = ctypes.CDLL(_LIB32)
+            _declare_sim(lib, ctypes.c_float)
+            _lib32 = lib
+    return _lib32
 
 
 def oracle_lib():
@@ -62,16 +96,7 @@ def oracle_lib():
             lib = ctypes.CDLL(build_oracle())
             P = ctypes.POINTER
             d = ctypes.c_double
-            lib.or_create.restype = ctypes.c_void_p
-            lib.or_create.argtypes = [P(params_struct)]
-            lib.or_destroy.argtypes = [ctypes.c_void_p]
-            lib.or_set_phi.argtypes = [ctypes.c_void_p, P(d)]
-            lib.or_step.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]
-            lib.or_get_moments.argtypes = [ctypes.c_void_p, P(d), P(d), P(d)]
-            lib.or_phase_mass.argtypes = [ctypes.c_void_p, P(d)]
-            lib.or_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, P(d)]
-            lib.or_steps_done.restype = ctypes.c_longlong
-            lib.or_steps_done.argtypes = [ctypes.c_void_p]
+            _declare_sim(lib, d)
             lib.or_field_grad.argtypes = [P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, P(d)]
             lib.or_field_lap.argtypes = lib.or_field_grad.argtypes
@@ -82,7 +107,6 @@ def oracle_lib():
             lib.or_phase_src.argtypes = [d, d, d, d, P(d)]
             lib.or_flow_geq.argtypes = [d, d, d, d, d, d, d, P(d)]
             lib.or_flow_force.argtypes = [d, d, d, P(d), P(d)]
-            lib.or_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -113,8 +137,13 @@ class OracleSim:
     """One FP64 oracle simulation.  ``phi0`` holds phases 1..N-1 as
     [N-1, ny, nx]; phase N is 1 - sum."""
 
-    def __init__(self, p: dict, phi0: np.ndarray, solve_all: bool = False, threads: int = 0):
-        self.lib = oracle_lib()
+    def __init__(self, p: dict, phi0: np.ndarray, solve_all: bool = False, threads: int = 0,
+                 fp32: bool = False):
+        """fp32=True runs the FP32 noise-model build instead of the oracle."""
+        self.fp32 = fp32
+        self.lib = oracle_lib_fp32() if fp32 else oracle_lib()
+        self._dt = np.float32 if fp32 else np.float64
+        self._ct = ctypes.c_float if fp32 else ctypes.c_double
         self.p = dict(p)
         self.N, self.nx, self.ny = int(p["n_phases"]), int(p["nx"]), int(p["ny"])
         self.threads = threads
@@ -122,9 +151,9 @@ class OracleSim:
         self.h = self.lib.or_create(ctypes.byref(self._ps))
         if not self.h:
             raise ValueError("oracle rejected the parameters")
-        phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        phi0 = np.ascontiguousarray(phi0, dtype=self._dt)
         assert phi0.shape == (self.N - 1, self.ny, self.nx), phi0.shape
-        self.lib.or_set_phi(self.h, _dp(phi0))
+        self.lib.or_set_phi(self.h, self._p(phi0))
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -139,17 +168,21 @@ class OracleSim:
     def steps_done(self) -> int:
         return int(self.lib.or_steps_done(self.h))
 
+    def _p(self, a):
+        return a.ctypes.data_as(ctypes.POINTER(self._ct))
+
     def moments(self):
-        phi = np.empty((self.N, self.ny, self.nx))
-        u = np.empty((2, self.ny, self.nx))
-        P = np.empty((self.ny, self.nx))
-        self.lib.or_get_moments(self.h, _dp(phi), _dp(u), _dp(P))
-        return phi, u, P
+        """(phi [N,ny,nx], u [2,ny,nx], P [ny,nx]) as float64 arrays."""
+        phi = np.empty((self.N, self.ny, self.nx), dtype=self._dt)
+        u = np.empty((2, self.ny, self.nx), dtype=self._dt)
+        P = np.empty((self.ny, self.nx), dtype=self._dt)
+        self.lib.or_get_moments(self.h, self._p(phi), self._p(u), self._p(P))
+        return phi.astype(np.float64), u.astype(np.float64), P.astype(np.float64)
 
     def phase_mass(self) -> np.ndarray:
-        m = np.empty(self.N)
-        self.lib.or_phase_mass(self.h, _dp(m))
-        return m
+        m = np.empty(self.N, dtype=self._dt)
+        self.lib.or_phase_mass(self.h, self._p(m))
+        return m.astype(np.float64)
 
     def field(self, name: str) -> np.ndarray:
         N, ny, nx = self.N, self.ny, self.nx
@@ -157,9 +190,9 @@ class OracleSim:
             "R": (0, (N, 2, ny, nx)), "mphi": (1, (2, ny, nx)), "muphi": (2, (N, ny, nx)),
             "F": (3, (2, ny, nx)), "grad": (4, (N, 2, ny, nx)), "lap": (5, (N, ny, nx)),
         }[name]
-        out = np.empty(shape)
-        self.lib.or_get_field(self.h, which, _dp(out))
-        return out
+        out = np.empty(shape, dtype=self._dt)
+        self.lib.or_get_field(self.h, which, self._p(out))
+        return out.astype(np.float64)
 
 
 # ---------------------------------------------------------------- field pins

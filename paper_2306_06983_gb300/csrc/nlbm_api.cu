@@ -1,0 +1,460 @@
+// Host side of the C ABI declared in include/nlbm.h: parameter validation,
+// workspace layout, kernel dispatch and checkpoints.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/nlbm.h"
+#include "nlbm_internal.cuh"
+
+using namespace nlbm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+constexpr size_t kMaxPlane = (size_t)1 << 28;   // keeps 9 * plane in 32-bit offsets
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t f[2], g[2], phi, u[2], mphi, P, partials, mass, total;
+};
+
+Layout make_layout(int ns, size_t plane)
+{
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.f[0] = take(sizeof(float) * ns * 9 * plane);
+    L.f[1] = take(sizeof(float) * ns * 9 * plane);
+    L.g[0] = take(sizeof(float) * 8 * plane);
+    L.g[1] = take(sizeof(float) * 8 * plane);
+    L.phi = take(sizeof(float) * ns * plane);
+    L.u[0] = take(sizeof(float) * 2 * plane);
+    L.u[1] = take(sizeof(float) * 2 * plane);
+    L.mphi = take(sizeof(float) * 2 * plane);
+    L.P = take(sizeof(float) * plane);
+    L.partials = take(sizeof(double) * kMassBlocks * (ns + 2));
+    L.mass = take(sizeof(double) * (ns + 2) + sizeof(int));
+    L.total = off;
+    return L;
+}
+
+void set_err(char *buf, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Validates the problem statement; fills the derived kernel parameters.
+nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
+{
+    if (!p) { set_err(err, "params is NULL"); return NLBM_EINVAL; }
+    const int N = p->n_phases;
+    if (N < 2 || N > kMaxPhases) { set_err(err, "n_phases=%d outside 2..%d", N, kMaxPhases); return NLBM_EINVAL; }
+    if (p->nx < 1 || p->ny < 1) { set_err(err, "lattice %dx%d is empty", p->nx, p->ny); return NLBM_EINVAL; }
+    if ((p->bc_x != NLBM_BC_PERIODIC && p->bc_x != NLBM_BC_WALL) ||
+        (p->bc_y != NLBM_BC_PERIODIC && p->bc_y != NLBM_BC_WALL)) {
+        set_err(err, "unknown boundary type"); return NLBM_EINVAL;
+    }
+    if ((p->bc_x == NLBM_BC_WALL && p->nx < 4) || (p->bc_y == NLBM_BC_WALL && p->ny < 4)) {
+        set_err(err, "a wall axis needs at least 4 nodes"); return NLBM_EINVAL;
+    }
+    if ((size_t)p->nx * (size_t)p->ny > kMaxPlane) {
+        set_err(err, "lattice of %zu nodes exceeds %zu", (size_t)p->nx * p->ny, kMaxPlane);
+        return NLBM_EINVAL;
+    }
+    if (p->model != NLBM_MODEL_A && p->model != NLBM_MODEL_B) { set_err(err, "unknown model"); return NLBM_EINVAL; }
+    if (p->model == NLBM_MODEL_A && !finite_pos(p->model_a_n)) { set_err(err, "Model A exponent n must be > 0"); return NLBM_EINVAL; }
+    if (!finite_pos(p->eps)) { set_err(err, "eps must be > 0"); return NLBM_EINVAL; }
+    if (!finite_pos(p->mobility)) { set_err(err, "mobility must be > 0"); return NLBM_EINVAL; }
+    if (!p->rho || !p->mu || !p->sigma) { set_err(err, "rho, mu and sigma must be given"); return NLBM_EINVAL; }
+    for (int a = 0; a < N; ++a) {
+        if (!finite_pos(p->rho[a])) { set_err(err, "rho[%d] must be > 0", a); return NLBM_EINVAL; }
+        if (!finite_pos(p->mu[a])) { set_err(err, "mu[%d] must be > 0", a); return NLBM_EINVAL; }
+        for (int b = 0; b < N; ++b) {
+            const double s = p->sigma[a * N + b];
+            if (a == b && s != 0.0) { set_err(err, "sigma[%d][%d] must be 0", a, a); return NLBM_EINVAL; }
+            if (a != b && !finite_pos(s)) { set_err(err, "sigma[%d][%d] must be > 0", a, b); return NLBM_EINVAL; }
+            if (s != p->sigma[b * N + a]) { set_err(err, "sigma is not symmetric at (%d,%d)", a, b); return NLBM_EINVAL; }
+        }
+    }
+    if (p->reserved != 0) { set_err(err, "reserved must be 0"); return NLBM_EINVAL; }
+    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) { set_err(err, "gravity not finite"); return NLBM_EINVAL; }
+    if (p->gx != 0.0 || p->gy != 0.0) { set_err(err, "gravity is not supported"); return NLBM_ENOTSUP; }
+    if (p->storage == NLBM_STORE_BF16 || p->storage == NLBM_STORE_F16) {
+        set_err(err, "reduced-precision storage is not supported by this build"); return NLBM_ENOTSUP;
+    }
+    if (p->storage != NLBM_STORE_F32) { set_err(err, "unknown storage"); return NLBM_EINVAL; }
+    if (kp) {
+        memset(kp, 0, sizeof *kp);
+        kp->nx = p->nx;
+        kp->ny = p->ny;
+        kp->wall_x = p->bc_x == NLBM_BC_WALL;
+        kp->wall_y = p->bc_y == NLBM_BC_WALL;
+        kp->plane = (unsigned)((size_t)p->nx * p->ny);
+        const double rhoN = p->rho[N - 1], muN = p->mu[N - 1];
+        kp->rhoN = (float)rhoN;
+        kp->muN = (float)muN;
+        for (int a = 0; a < N - 1; ++a) {
+            kp->drho[a] = (float)(p->rho[a] - rhoN);
+            kp->dmu[a] = (float)(p->mu[a] - muN);
+        }
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) {
+                const double s = p->sigma[a * N + b];
+                kp->beta2[a][b] = (float)(6.0 * s / p->eps);       // 2 beta_pq, Eq. (15)
+                kp->kap[a][b] = (float)(0.75 * p->eps * s);        // -k_pq, Eq. (15)
+            }
+        kp->four_over_eps = (float)(4.0 / p->eps);
+        kp->mob = (float)p->mobility;
+        kp->s1 = (float)(1.0 / (0.5 + 3.0 * p->mobility));        // Eq. (20), c_s^2 = 1/3
+        kp->model_n = (float)p->model_a_n;
+        const double n = p->model_a_n;
+        kp->model_n_int = (n == std::floor(n) && n >= 1.0 && n <= 8.0) ? (int)n : 0;
+    }
+    return NLBM_OK;
+}
+
+}  // namespace
+
+struct nlbm_sim {
+    StepParams kp;
+    int N, ns, model;
+    size_t plane;
+    cudaStream_t stream;
+    char *ws;
+    Layout L;
+    int cur;
+    int64_t steps;
+    int64_t launches;
+    int tx, ty;
+    char err[512];
+    float *f(int k) const { return (float *)(ws + L.f[k]); }
+    float *g(int k) const { return (float *)(ws + L.g[k]); }
+    float *u(int k) const { return (float *)(ws + L.u[k]); }
+    float *phi() const { return (float *)(ws + L.phi); }
+    float *mphi() const { return (float *)(ws + L.mphi); }
+    float *P() const { return (float *)(ws + L.P); }
+};
+
+namespace {
+
+nlbm_status cuda_fail(nlbm_sim *s, cudaError_t e, const char *what)
+{
+    set_err(s->err, "%s: %s", what, cudaGetErrorString(e));
+    return NLBM_ECUDA;
+}
+
+void default_tile(nlbm_sim *s)
+{
+    int tx = 128;
+    while (tx > 32 && tx / 2 >= s->kp.nx) tx /= 2;
+    s->tx = tx;
+    s->ty = 32;
+}
+
+// Number of state bytes in a checkpoint, excluding the trailing counter.
+size_t state_payload(const nlbm_sim *s)
+{
+    return sizeof(float) * s->plane * ((size_t)s->ns * 9 + 8 + 2 + s->ns + 2 + 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes)
+{
+    if (!bytes) { set_err(g_err, "bytes is NULL"); return NLBM_EINVAL; }
+    nlbm_status st = validate(p, nullptr, g_err);
+    if (st != NLBM_OK) return st;
+    *bytes = make_layout(p->n_phases - 1, (size_t)p->nx * p->ny).total;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t workspace_bytes,
+                        void *cuda_stream, nlbm_sim **out)
+{
+    if (!out) { set_err(g_err, "out is NULL"); return NLBM_EINVAL; }
+    *out = nullptr;
+    StepParams kp;
+    nlbm_status st = validate(p, &kp, g_err);
+    if (st != NLBM_OK) return st;
+    const int ns = p->n_phases - 1;
+    const Layout L = make_layout(ns, (size_t)p->nx * p->ny);
+    if (!dev_workspace) { set_err(g_err, "workspace is NULL"); return NLBM_EINVAL; }
+    if (((uintptr_t)dev_workspace & 255) != 0) { set_err(g_err, "workspace must be 256-byte aligned"); return NLBM_EINVAL; }
+    if (workspace_bytes < L.total) {
+        set_err(g_err, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, L.total);
+        return NLBM_ENOMEM;
+    }
+    nlbm_sim *s = new (std::nothrow) nlbm_sim();
+    if (!s) { set_err(g_err, "host allocation failed"); return NLBM_ENOMEM; }
+    s->kp = kp;
+    s->N = p->n_phases;
+    s->ns = ns;
+    s->model = p->model;
+    s->plane = (size_t)p->nx * p->ny;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->ws = (char *)dev_workspace;
+    s->L = L;
+    s->cur = 0;
+    s->steps = 0;
+    s->launches = 0;
+    s->err[0] = 0;
+    default_tile(s);
+    *out = s;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi)
+{
+    if (!s || !dev_phi) return NLBM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(s->phi(), dev_phi, sizeof(float) * s->ns * s->plane,
+                                    cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy of the initial phase fields");
+    StepParams kp = s->kp;
+    s->cur = 0;
+    kp.fout = s->f(0);
+    kp.gout = s->g(0);
+    kp.uout = s->u(0);
+    kp.uin = s->u(1);
+    kp.phi = s->phi();
+    kp.mphi = s->mphi();
+    kp.pout = s->P();
+    e = launch_init(s->ns, kp, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
+    s->launches++;
+    s->steps = 0;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
+{
+    if (!s || !host_phi) return NLBM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(s->phi(), host_phi, sizeof(float) * s->ns * s->plane,
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "upload of the initial phase fields");
+    // the device copy in the phi planes is its own source for the init kernel
+    StepParams kp = s->kp;
+    s->cur = 0;
+    kp.fout = s->f(0);
+    kp.gout = s->g(0);
+    kp.uout = s->u(0);
+    kp.uin = s->u(1);
+    kp.phi = s->phi();
+    kp.mphi = s->mphi();
+    kp.pout = s->P();
+    e = launch_init(s->ns, kp, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
+    s->launches++;
+    s->steps = 0;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_step(nlbm_sim *s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return NLBM_EINVAL;
+    int ty = s->ty;
+    const int min_ty = (s->kp.ny + 65534) / 65535;   // grid.y limit
+    if (ty < min_ty) ty = min_ty;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        StepParams kp = s->kp;
+        const int a = s->cur, b = s->cur ^ 1;
+        kp.fin = s->f(a);
+        kp.fout = s->f(b);
+        kp.gin = s->g(a);
+        kp.gout = s->g(b);
+        kp.uin = s->u(a);
+        kp.uout = s->u(b);
+        kp.phi = s->phi();
+        kp.mphi = s->mphi();
+        kp.pout = (k == nsteps - 1) ? s->P() : nullptr;
+        cudaError_t e = s->model == NLBM_MODEL_A ? launch_step_model_a(s->ns, kp, s->tx, ty, s->stream)
+                                                 : launch_step_model_b(s->ns, kp, s->tx, ty, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "step kernel");
+        s->launches++;
+        s->cur = b;
+        s->steps++;
+    }
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_get_moments(nlbm_sim *s, float *dev_phi, float *dev_u, float *dev_p)
+{
+    if (!s) return NLBM_EINVAL;
+    if (!dev_phi && !dev_u && !dev_p) return NLBM_OK;
+    cudaError_t e = launch_export(s->ns, s->phi(), s->u(s->cur), s->P(), (unsigned)s->plane, dev_phi,
+                                  dev_u, dev_p, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "export kernel");
+    s->launches++;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_get_moments_host(nlbm_sim *s, float *host_phi, float *host_u, float *host_p)
+{
+    if (!s) return NLBM_EINVAL;
+    if (!host_phi && !host_u && !host_p) return NLBM_OK;
+    // Stage through the idle population buffer (it is rewritten by the next
+    // step): N + 3 planes fit in the 9 (N-1) planes of one f copy.
+    const size_t pl = s->plane, pb = sizeof(float) * pl;
+    float *stage = s->f(s->cur ^ 1);
+    float *sphi = stage, *su = stage + (size_t)s->N * pl, *sp = su + 2 * pl;
+    cudaError_t e = launch_export(s->ns, s->phi(), s->u(s->cur), s->P(), (unsigned)pl,
+                                  host_phi ? sphi : nullptr, host_u ? su : nullptr,
+                                  host_p ? sp : nullptr, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "export kernel");
+    s->launches++;
+    if (host_phi && (e = cudaMemcpyAsync(host_phi, sphi, pb * s->N, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess)
+        return cuda_fail(s, e, "download of phi");
+    if (host_u && (e = cudaMemcpyAsync(host_u, su, 2 * pb, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess)
+        return cuda_fail(s, e, "download of u");
+    if (host_p && (e = cudaMemcpyAsync(host_p, sp, pb, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess)
+        return cuda_fail(s, e, "download of P");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_phase_mass(nlbm_sim *s, double *host_mass)
+{
+    if (!s || !host_mass) return NLBM_EINVAL;
+    double *partials = (double *)(s->ws + s->L.partials);
+    double *mass = (double *)(s->ws + s->L.mass);
+    int *flag = (int *)(mass + s->N);
+    cudaError_t e = launch_phase_mass(s->ns, s->phi(), (unsigned)s->plane, partials, mass, flag, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase-mass kernels");
+    s->launches += 2;
+    double buf[kMaxPhases + 1];
+    e = cudaMemcpyAsync(buf, mass, sizeof(double) * s->N + sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "download of the phase masses");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+    memcpy(host_mass, buf, sizeof(double) * s->N);
+    int fl = 0;
+    memcpy(&fl, (const char *)buf + sizeof(double) * s->N, sizeof(int));
+    if (fl) {
+        set_err(s->err, "a phase field is non-finite or outside [-0.5, 1.5]");
+        return NLBM_EDIVERGED;
+    }
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_state_bytes(const nlbm_sim *s, size_t *bytes)
+{
+    if (!s || !bytes) return NLBM_EINVAL;
+    *bytes = state_payload(s) + 16;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_save(nlbm_sim *s, void *dev_dst)
+{
+    if (!s || !dev_dst || ((uintptr_t)dev_dst & 15)) return NLBM_EINVAL;
+    char *d = (char *)dev_dst;
+    const size_t pb = sizeof(float) * s->plane;
+    struct Part { const void *src; size_t n; } parts[] = {
+        {s->f(s->cur), pb * s->ns * 9}, {s->g(s->cur), pb * 8}, {s->u(s->cur), pb * 2},
+        {s->phi(), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(), pb}};
+    for (const Part &pt : parts) {
+        cudaError_t e = cudaMemcpyAsync(d, pt.src, pt.n, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "checkpoint copy");
+        d += pt.n;
+    }
+    int64_t counter[2] = {s->steps, 0x6e6c626d};   // step count and a tag
+    cudaError_t e = cudaMemcpyAsync(d, counter, sizeof counter, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "checkpoint counter");
+    e = cudaStreamSynchronize(s->stream);   // counter is a host stack value
+    if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_restore(nlbm_sim *s, const void *dev_src)
+{
+    if (!s || !dev_src || ((uintptr_t)dev_src & 15)) return NLBM_EINVAL;
+    const char *d = (const char *)dev_src;
+    const size_t pb = sizeof(float) * s->plane;
+    s->cur = 0;
+    struct Part { void *dst; size_t n; } parts[] = {
+        {s->f(0), pb * s->ns * 9}, {s->g(0), pb * 8}, {s->u(0), pb * 2},
+        {s->phi(), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(), pb}};
+    for (const Part &pt : parts) {
+        cudaError_t e = cudaMemcpyAsync(pt.dst, d, pt.n, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "restore copy");
+        d += pt.n;
+    }
+    int64_t counter[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(counter, d, sizeof counter, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "restore counter");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+    if (counter[1] != 0x6e6c626d) {
+        set_err(s->err, "checkpoint tag mismatch");
+        return NLBM_EINVAL;
+    }
+    s->steps = counter[0];
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_synchronize(nlbm_sim *s)
+{
+    if (!s) return NLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+    return NLBM_OK;
+}
+
+int64_t nlbm_steps_done(const nlbm_sim *s) { return s ? s->steps : -1; }
+
+int64_t nlbm_kernel_launches(const nlbm_sim *s) { return s ? s->launches : -1; }
+
+nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty)
+{
+    if (!s) return NLBM_EINVAL;
+    if (tx < 32 || tx > 256 || tx % 32 != 0 || ty < 1) {
+        set_err(s->err, "tile %dx%d outside tx in {32..256, multiple of 32}, ty >= 1", tx, ty);
+        return NLBM_EINVAL;
+    }
+    s->tx = tx;
+    s->ty = ty;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty)
+{
+    if (!s || !tx || !ty) return NLBM_EINVAL;
+    *tx = s->tx;
+    *ty = s->ty;
+    return NLBM_OK;
+}
+
+void nlbm_destroy(nlbm_sim *s) { delete s; }
+
+const char *nlbm_last_error(const nlbm_sim *s) { return s ? s->err : g_err; }
+
+const char *nlbm_status_string(nlbm_status st)
+{
+    switch (st) {
+    case NLBM_OK: return "ok";
+    case NLBM_EINVAL: return "invalid argument";
+    case NLBM_ENOMEM: return "insufficient memory";
+    case NLBM_ECUDA: return "CUDA error";
+    case NLBM_ENOTSUP: return "not supported";
+    case NLBM_EDIVERGED: return "diverged";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Internal declarations shared by the CUDA translation units of libnlbm.
+//
+// Lattice: D2Q9 with the velocity order of the columns of the moment matrix
+// in Eq. (28): c0 = (0,0), c1 = (1,0), c2 = (0,1), c3 = (-1,0), c4 = (0,-1),
+// c5 = (1,1), c6 = (-1,1), c7 = (-1,-1), c8 = (1,-1); weights 4/9, 1/9, 1/36;
+// c_s^2 = 1/3 (Sec. 4).
+//
+// Storage (structure of arrays, one plane = nx*ny floats, row-major):
+//   f  [N-1][9][plane]  post-collision phase populations (pull streaming:
+//                       node x reads f*_i(x - c_i) of the previous step)
+//   g  [8][plane]       post-collision flow populations g_1..g_8; g_0 is
+//                       never stored: rows 1..8 of M^-1 have a zero in
+//                       column 0, so g_0 feeds neither u (c_0 = 0) nor P
+//                       (Eq. (25c) sums i != 0) nor any later g_i.
+//   phi [N-1][plane]    phi_p of the last step (the "previous" value for the
+//                       backward-Euler time derivatives of the next step)
+//   u   [2][plane]      velocity of the last step (double-buffered: the next
+//                       step reads it at neighbours for F_c)
+//   mphi [2][plane]     m_phi of the last step
+//   P   [plane]         pressure, written on request
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nlbm {
+
+constexpr int kMaxPhases = 8;
+
+struct StepParams {
+    int nx, ny;
+    int wall_x, wall_y;
+    unsigned plane;            // floats per field plane (nx*ny)
+    float drho[kMaxPhases];    // rho_p - rho_N, p = 1..N-1
+    float rhoN;
+    float dmu[kMaxPhases];     // mu_p - mu_N
+    float muN;
+    float beta2[kMaxPhases][kMaxPhases];  // 2 beta_pq = 6 sigma_pq / eps (Eq. (15))
+    float kap[kMaxPhases][kMaxPhases];    // -k_pq = 3 eps sigma_pq / 4 (Eq. (15))
+    float four_over_eps;       // 4 / eps
+    float mob;                 // M
+    float s1;                  // 1 / tau_f, tau_f = 0.5 + 3 M (Eq. (20))
+    float model_n;             // Model A exponent n
+    int model_n_int;           // n when it is an integer in 1..8, else 0
+    const float *fin;
+    float *fout;
+    const float *gin;
+    float *gout;
+    float *phi;                // [N-1][plane] in: previous step, out: this step
+    const float *uin;          // [2][plane] previous step
+    float *uout;               // [2][plane] this step
+    float *mphi;               // [2][plane] in: previous step, out: this step
+    float *pout;               // [plane] or nullptr
+};
+
+// Launchers (defined in step_model_a.cu / step_model_b.cu).  smem bytes and
+// grid are computed by the launcher; returns the launch error.
+cudaError_t launch_step_model_a(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_model_b(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+
+// Auxiliary kernels (aux_kernels.cu).
+cudaError_t launch_init(int ns, const StepParams &p, cudaStream_t st);
+cudaError_t launch_export(int ns, const float *phi_aux, const float *u, const float *P,
+                          unsigned plane, float *phi_out, float *u_out, float *p_out,
+                          cudaStream_t st);
+constexpr int kMassBlocks = 512;   // fixed grid: the reduction order is fixed
+cudaError_t launch_phase_mass(int ns, const float *phi_aux, unsigned plane, double *partials,
+                              double *mass_out, int *flag_out, cudaStream_t st);
+
+}  // namespace nlbm

@@ -1,0 +1,591 @@
+// The fused per-step kernel: pull streaming, phase fields, isotropic stencils,
+// Model A / Model B sources, consistent mass flux, surface tension, F_c,
+// velocity, pressure and both MRT collisions in one pass over the lattice.
+//
+// Work decomposition.  A thread block owns a strip of TX consecutive columns
+// (one thread per column) and marches down TY rows.  The update of row r
+// needs phi(t) on rows r-2..r+2 (F_c differentiates m_phi, which
+// differentiates phi) and m_phi on rows r-1..r+1, so each iteration runs
+// three stages on a rolling window kept in shared memory:
+//   A (row r+2): pull the phase populations, phi_p = sum_i f_i (Eq. (25a)),
+//                for the strip plus two halo columns each side; keep the
+//                first moments j_p of the strip's own nodes;
+//   B (row r+1): grad phi (Eq. (27)), source R_p (Eqs. (2)-(4)) and
+//                m_phi = -M sum_p rho_p (grad phi_p - R_p) (Eq. (13)) for the
+//                strip plus one halo column each side; stage the previous
+//                step's velocity of that row;
+//   C (row r):   Laplacians, chemical potentials and F_s (Eqs. (16)-(17)),
+//                F_c, pull of the flow populations, u and P (Eqs. (25b),
+//                (25c)), both collisions (Eqs. (18)-(24)), stores.
+// Only the halo columns and the 4 + 2 pre-roll rows per strip are computed
+// twice; every population is read from HBM once and written once.
+//
+// Collision in closed form.  With the relaxation matrix of Sec. 4
+// (S = diag(s0, s1, s1, s2, s2, s2, s3, s3, s4), all entries 1 except
+// s1 = 1/tau_f for the phase field and s2 = 1/tau_g for the flow), every
+// post-collision moment of order >= 2 of a phase set is its equilibrium plus
+// half its source moment, so f* depends on the pulled f only through
+// phi = sum f_i and j = sum c_i f_i.  For the flow set the pulled g enters
+// through j_g, the second moments Pi and sum_{i!=0} g_i.  The inverse of the
+// moment matrix of Eq. (28) is applied in closed form.
+#pragma once
+
+#include "nlbm_internal.cuh"
+
+namespace nlbm {
+
+__device__ __forceinline__ int map_axis(int c, int n, int wall, bool &flip)
+{
+    flip = false;
+    if (c >= 0 && c < n) return c;
+    if (!wall) {
+        c %= n;
+        if (c < 0) c += n;
+        return c;
+    }
+    flip = true;                       // half-way wall: mirror image node
+    return c < 0 ? -1 - c : 2 * n - 1 - c;
+}
+
+__device__ __forceinline__ int slot5(int r) { return (r + 10) % 5; }
+__device__ __forceinline__ int slot3(int r) { return (r + 9) % 3; }
+__device__ __forceinline__ int slot2(int r) { return (r + 8) & 1; }
+
+// Sources of the pull at node (x, y): direction i of this node comes from
+// node[i] in plane dir[i] (dir[i] = i, or the opposite direction of the own
+// node when the link crosses a half-way bounce-back wall).
+__device__ __forceinline__ void pull_sources(const StepParams &P, int x, int y,
+                                             unsigned (&node)[9], int (&dir)[9])
+{
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1;
+    bool oxm = false, oxp = false, oym = false, oyp = false;
+    if (xm < 0) { if (P.wall_x) oxm = true; else xm += P.nx; }
+    if (xp >= P.nx) { if (P.wall_x) oxp = true; else xp -= P.nx; }
+    if (ym < 0) { if (P.wall_y) oym = true; else ym += P.ny; }
+    if (yp >= P.ny) { if (P.wall_y) oyp = true; else yp -= P.ny; }
+    const unsigned nx = (unsigned)P.nx;
+    const unsigned self = (unsigned)y * nx + x;
+    const unsigned r0 = (unsigned)y * nx, rm = (unsigned)ym * nx, rp = (unsigned)yp * nx;
+    node[0] = self; dir[0] = 0;
+    // f_i(x) = f*_i(x - c_i)
+    if (oxm) { node[1] = self; dir[1] = 3; } else { node[1] = r0 + xm; dir[1] = 1; }
+    if (oym) { node[2] = self; dir[2] = 4; } else { node[2] = rm + x; dir[2] = 2; }
+    if (oxp) { node[3] = self; dir[3] = 1; } else { node[3] = r0 + xp; dir[3] = 3; }
+    if (oyp) { node[4] = self; dir[4] = 2; } else { node[4] = rp + x; dir[4] = 4; }
+    if (oxm || oym) { node[5] = self; dir[5] = 7; } else { node[5] = rm + xm; dir[5] = 5; }
+    if (oxp || oym) { node[6] = self; dir[6] = 8; } else { node[6] = rm + xp; dir[6] = 6; }
+    if (oxp || oyp) { node[7] = self; dir[7] = 5; } else { node[7] = rp + xp; dir[7] = 7; }
+    if (oxm || oyp) { node[8] = self; dir[8] = 6; } else { node[8] = rp + xm; dir[8] = 8; }
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum, 6 flops).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// Pulled phase fields at one node.  phi = f_0 + f_1 + ... + f_8 is summed in
+// this fixed order everywhere (own and halo nodes give identical bits).  For
+// the strip's own nodes the rounding error of that sum (phi_lo, exact when
+// the running sum dominates each term, as the rest population does) and the
+// first moments j_p are returned as well.
+template <int NS, bool OWN>
+__device__ __forceinline__ void pull_phi(const StepParams &P, int x, int y, float (&ph)[NS],
+                                         float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
+{
+    unsigned node[9];
+    int dir[9];
+    pull_sources(P, x, y, node, dir);
+    const unsigned pl = P.plane;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float *__restrict__ fp = P.fin + (size_t)p * 9 * pl;
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = __ldg(fp + (unsigned)dir[i] * pl + node[i]);
+        float s = f[0], e = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float t = s + f[i];
+            if (OWN) e += f[i] - (t - s);     // Fast2Sum error term
+            s = t;
+        }
+        ph[p] = s;
+        if (OWN) {
+            plo[p] = e;
+            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        }
+    }
+}
+
+// Two populations c + h and c - h whose stored values sum to exactly 2c:
+// the larger is rounded, the smaller is 2c minus it (exact by Sterbenz's
+// lemma whenever |h| <= 3|c|, which holds away from vanishing phase fields).
+__device__ __forceinline__ void exact_pair(float c, float h, float &plus, float &minus)
+{
+    const float big = c + fabsf(h);
+    const float small = (c + c) - big;
+    plus = h >= 0.f ? big : small;
+    minus = h >= 0.f ? small : big;
+}
+
+// Unit vector with the zero-gradient reading: 0 when |v|^2 <= 1e-24.
+__device__ __forceinline__ float inv_norm(float vx, float vy)
+{
+    const float n2 = vx * vx + vy * vy;
+    return n2 > 1e-24f ? rsqrtf(n2) : 0.0f;
+}
+
+// 3x3 window of the phase fields in the ring: phi, grad phi (Eq. (27)) for
+// all N phases (phase N by phi_N = 1 - sum, grad phi_N = -sum).
+template <int NS>
+__device__ __forceinline__ void window_grad(const float *s_phi, int W, int sm, int s0, int sp,
+                                            int c, float (&ph)[NS + 1], float (&gx)[NS + 1],
+                                            float (&gy)[NS + 1])
+{
+    float sph = 0.f, sgx = 0.f, sgy = 0.f;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float *rm = s_phi + (sm * NS + p) * W + c;
+        const float *r0 = s_phi + (s0 * NS + p) * W + c;
+        const float *rp = s_phi + (sp * NS + p) * W + c;
+        const float sw = rm[-1], s = rm[0], se = rm[1];
+        const float w = r0[-1], ce = r0[0], e = r0[1];
+        const float nw = rp[-1], n = rp[0], ne = rp[1];
+        ph[p] = ce;
+        gx[p] = (e - w) * (1.f / 3.f) + ((ne + se) - (nw + sw)) * (1.f / 12.f);
+        gy[p] = (n - s) * (1.f / 3.f) + ((ne + nw) - (se + sw)) * (1.f / 12.f);
+        sph += ce;
+        sgx += gx[p];
+        sgy += gy[p];
+    }
+    ph[NS] = 1.f - sph;
+    gx[NS] = -sgx;
+    gy[NS] = -sgy;
+}
+
+// Laplacians (Eq. (27)) of the solved phases from the ring; phase N by -sum.
+template <int NS>
+__device__ __forceinline__ void window_lap(const float *s_phi, int W, int sm, int s0, int sp, int c,
+                                           float (&lap)[NS + 1])
+{
+    float sl = 0.f;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float *rm = s_phi + (sm * NS + p) * W + c;
+        const float *r0 = s_phi + (s0 * NS + p) * W + c;
+        const float *rp = s_phi + (sp * NS + p) * W + c;
+        const float ce = r0[0];
+        const float ax = ((r0[1] - ce) + (r0[-1] - ce)) + ((rp[0] - ce) + (rm[0] - ce));
+        const float dg = ((rp[1] - ce) + (rp[-1] - ce)) + ((rm[1] - ce) + (rm[-1] - ce));
+        lap[p] = ax * (2.f / 3.f) + dg * (1.f / 6.f);
+        sl += lap[p];
+    }
+    lap[NS] = -sl;
+}
+
+// Source R_p of the solved phases (Eqs. (2)-(4)).
+template <int NS, int MODEL>
+__device__ __forceinline__ void source_terms(const StepParams &P, const float (&ph)[NS + 1],
+                                             const float (&gx)[NS + 1], const float (&gy)[NS + 1],
+                                             float (&Rx)[NS], float (&Ry)[NS])
+{
+    constexpr int N = NS + 1;
+    if (MODEL == 0) {
+        // Model A, Eq. (2): R_p = a_p n_p - phi_p^n / sum_q phi_q^n * sum_q a_q n_q
+        float a[N], nxv[N], nyv[N], w[N];
+        float S = 0.f, Vx = 0.f, Vy = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            a[q] = P.four_over_eps * ph[q] * (1.f - ph[q]);
+            const float r = inv_norm(gx[q], gy[q]);
+            nxv[q] = gx[q] * r;
+            nyv[q] = gy[q] * r;
+            const float pc = fmaxf(ph[q], 0.f);
+            float wq;
+            if (P.model_n_int == 1) {
+                wq = pc;
+            } else if (P.model_n_int == 2) {
+                wq = pc * pc;
+            } else if (P.model_n_int > 2) {
+                wq = pc;
+                for (int k = 1; k < P.model_n_int; ++k) wq *= pc;
+            } else {
+                wq = powf(pc, P.model_n);
+            }
+            w[q] = wq;
+            S += wq;
+            Vx += a[q] * nxv[q];
+            Vy += a[q] * nyv[q];
+        }
+        const float invS = 1.f / S;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            const float b = w[p] * invS;
+            Rx[p] = a[p] * nxv[p] - b * Vx;
+            Ry[p] = a[p] * nyv[p] - b * Vy;
+        }
+    } else {
+        // Model B, Eqs. (3)-(4): R_p = sum_{q!=p} 4 phi_p phi_q / eps n_pq,
+        // n_pq = unit(phi_q grad phi_p - phi_p grad phi_q), n_qp = -n_pq.
+#pragma unroll
+        for (int p = 0; p < NS; ++p) { Rx[p] = 0.f; Ry[p] = 0.f; }
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                const float vx = ph[q] * gx[p] - ph[p] * gx[q];
+                const float vy = ph[q] * gy[p] - ph[p] * gy[q];
+                const float c = P.four_over_eps * ph[p] * ph[q] * inv_norm(vx, vy);
+                if (p < NS) { Rx[p] += c * vx; Ry[p] += c * vy; }
+                if (q < NS) { Rx[q] -= c * vx; Ry[q] -= c * vy; }
+            }
+        }
+    }
+}
+
+// Consistent mass flux, Eq. (13), with phase N eliminated:
+// m_phi = -M sum_{p<N} (rho_p - rho_N) (grad phi_p - R_p).
+template <int NS>
+__device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)[NS + 1],
+                                          const float (&gy)[NS + 1], const float (&Rx)[NS],
+                                          const float (&Ry)[NS], float &mx, float &my)
+{
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        ax += P.drho[p] * (gx[p] - Rx[p]);
+        ay += P.drho[p] * (gy[p] - Ry[p]);
+    }
+    mx = -P.mob * ax;
+    my = -P.mob * ay;
+}
+
+template <int NS, int MODEL>
+__global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int TY)
+{
+    constexpr int N = NS + 1;
+    extern __shared__ float smem[];
+    const int TX = blockDim.x;
+    const int WP = TX + 4, WM = TX + 2;
+    float *s_phi = smem;                     // [5][NS][WP]  phi(t) rows r-2..r+2
+    float *s_m = s_phi + 5 * NS * WP;        // [3][2][WM]   m_phi(t) rows r-1..r+1
+    float *s_u = s_m + 6 * WM;               // [3][2][WM]   u(t-1)   rows r-1..r+1
+    float *s_j = s_u + 6 * WM;               // [3][3NS][TX] j_x, j_y, phi_lo of own nodes
+    float *s_R = s_j + 9 * NS * TX;          // [2][2NS][TX] sources of own nodes
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int TXe = min(TX, P.nx - x0), TYe = min(TY, P.ny - y0);
+    const bool active = tid < TXe;
+    const int xg = x0 + tid;
+    const unsigned pl = P.plane;
+    const int nx = P.nx;
+
+    for (int it = 0; it < TYe + 4; ++it) {
+        const int ra = y0 - 2 + it;
+        // ---------------------------------------------------- stage A
+        {
+            bool yflip;
+            const int ya = map_axis(ra, P.ny, P.wall_y, yflip);
+            const int s5 = slot5(ra);
+            if (active) {
+                float ph[NS], plo[NS], jx[NS], jy[NS];
+                const bool own_row = ra >= y0 && ra < y0 + TYe;
+                pull_phi<NS, true>(P, xg, ya, ph, plo, jx, jy);
+#pragma unroll
+                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + tid + 2] = ph[p];
+                if (own_row) {
+                    const int s3 = slot3(ra);
+#pragma unroll
+                    for (int p = 0; p < NS; ++p) {
+                        s_j[(s3 * 3 * NS + 3 * p) * TX + tid] = jx[p];
+                        s_j[(s3 * 3 * NS + 3 * p + 1) * TX + tid] = jy[p];
+                        s_j[(s3 * 3 * NS + 3 * p + 2) * TX + tid] = plo[p];
+                    }
+                }
+            }
+            if (tid < 4) {
+                const int lx = tid < 2 ? tid : TXe + tid;
+                bool xflip;
+                const int xx = map_axis(x0 - 2 + lx, nx, P.wall_x, xflip);
+                float ph[NS], plo[NS], jx[NS], jy[NS];
+                pull_phi<NS, false>(P, xx, ya, ph, plo, jx, jy);
+#pragma unroll
+                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + lx] = ph[p];
+            }
+        }
+        __syncthreads();
+        // ---------------------------------------------------- stage B
+        if (it >= 2) {
+            const int rb = ra - 1;
+            const int sm = slot5(rb - 1), s0 = slot5(rb), sp = slot5(rb + 1);
+            const int s3 = slot3(rb);
+            if (active) {
+                float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
+                window_grad<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy);
+                source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
+                mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
+                s_m[(s3 * 2 + 0) * WM + tid + 1] = mx;
+                s_m[(s3 * 2 + 1) * WM + tid + 1] = my;
+                if (rb >= y0 && rb < y0 + TYe) {
+                    const int s2 = slot2(rb);
+#pragma unroll
+                    for (int p = 0; p < NS; ++p) {
+                        s_R[(s2 * 2 * NS + 2 * p) * TX + tid] = Rx[p];
+                        s_R[(s2 * 2 * NS + 2 * p + 1) * TX + tid] = Ry[p];
+                    }
+                }
+            }
+            if (tid < 2) {
+                const int lm = tid == 0 ? 0 : TXe + 1;
+                float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
+                window_grad<NS>(s_phi, WP, sm, s0, sp, lm + 1, ph, gx, gy);
+                source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
+                mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
+                s_m[(s3 * 2 + 0) * WM + lm] = mx;
+                s_m[(s3 * 2 + 1) * WM + lm] = my;
+            }
+            bool yflip;
+            const int yb = map_axis(rb, P.ny, P.wall_y, yflip);
+            for (int lm = tid; lm < TXe + 2; lm += TX) {
+                bool xflip;
+                const int xb = map_axis(x0 - 1 + lm, nx, P.wall_x, xflip);
+                const unsigned k = (unsigned)yb * nx + xb;
+                float ux = __ldg(P.uin + k), uy = __ldg(P.uin + pl + k);
+                if (xflip != yflip) { ux = -ux; uy = -uy; }   // no-slip ghost
+                s_u[(s3 * 2 + 0) * WM + lm] = ux;
+                s_u[(s3 * 2 + 1) * WM + lm] = uy;
+            }
+        }
+        __syncthreads();
+        // ---------------------------------------------------- stage C
+        if (it >= 4 && active) {
+            const int y = ra - 2;
+            const unsigned node = (unsigned)y * nx + xg;
+            // previous-step values of this node
+            float php[NS];
+#pragma unroll
+            for (int p = 0; p < NS; ++p) php[p] = P.phi[(size_t)p * pl + node];
+            const float mpx = P.mphi[node], mpy = P.mphi[pl + node];
+            // pulled flow populations g_1..g_8
+            float g[9];
+            {
+                unsigned gnode[9];
+                int gdir[9];
+                pull_sources(P, xg, y, gnode, gdir);
+#pragma unroll
+                for (int i = 1; i < 9; ++i)
+                    g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+            }
+            const int sm = slot5(y - 1), s0 = slot5(y), sp = slot5(y + 1);
+            float ph[N], gx[N], gy[N], lap[N];
+            window_grad<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy);
+            window_lap<NS>(s_phi, WP, sm, s0, sp, tid + 2, lap);
+
+            // mixture density, viscosity and grad rho (Eqs. (11),(12))
+            float rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f;
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+                rho += P.drho[p] * ph[p];
+                mu += P.dmu[p] * ph[p];
+                grx += P.drho[p] * gx[p];
+                gry += P.drho[p] * gy[p];
+            }
+
+            // chemical potentials (Eq. (17)) and F_s = sum_p mu_p grad phi_p (Eq. (16))
+            float gp[N], muph[N];
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+                gp[p] = 2.f * ph[p] * (1.f - ph[p]) * (1.f - 2.f * ph[p]);
+                muph[p] = 0.f;
+            }
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+#pragma unroll
+                for (int q = p + 1; q < N; ++q) {
+                    const float s = ph[p] + ph[q];
+                    const float G = 2.f * s * (1.f - s) * (1.f - 2.f * s);
+                    const float b = P.beta2[p][q], k = P.kap[p][q];
+                    muph[p] += b * (gp[p] - G) + k * lap[q];
+                    muph[q] += b * (gp[q] - G) + k * lap[p];
+                }
+            }
+            float Fx = 0.f, Fy = 0.f;
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+                const float d = muph[p] - muph[NS];
+                Fx += d * gx[p];
+                Fy += d * gy[p];
+            }
+
+            // F_c = -div(m_phi u - u m_phi)/2 with the previous velocity:
+            // with w = m_x u_y - u_x m_y, F_c = (d_y w / 2, -d_x w / 2).
+            {
+                const int t3m = slot3(y - 1), t30 = slot3(y), t3p = slot3(y + 1);
+                const int c = tid + 1;
+                auto W = [&](int s, int cc) {
+                    const float mx = s_m[(s * 2) * WM + cc], my = s_m[(s * 2 + 1) * WM + cc];
+                    const float ux = s_u[(s * 2) * WM + cc], uy = s_u[(s * 2 + 1) * WM + cc];
+                    return mx * uy - ux * my;
+                };
+                const float wsw = W(t3m, c - 1), ws = W(t3m, c), wse = W(t3m, c + 1);
+                const float ww = W(t30, c - 1), we = W(t30, c + 1);
+                const float wnw = W(t3p, c - 1), wn = W(t3p, c), wne = W(t3p, c + 1);
+                const float dxw = (we - ww) * (1.f / 3.f) + ((wne + wse) - (wnw + wsw)) * (1.f / 12.f);
+                const float dyw = (wn - ws) * (1.f / 3.f) + ((wne + wnw) - (wse + wsw)) * (1.f / 12.f);
+                Fx += 0.5f * dyw;
+                Fy -= 0.5f * dxw;
+            }
+
+            // macroscopic velocity (Eq. (25b)) and mass flux (Eq. (13))
+            const float sg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+            const float jgx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+            const float jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+            const float d58 = (g[5] + g[6]) + (g[7] + g[8]);
+            const float Pxx = (g[1] + g[3]) + d58;
+            const float Pyy = (g[2] + g[4]) + d58;
+            const float Pxy = (g[5] - g[6]) + (g[7] - g[8]);
+            const float inv_rho = 1.f / rho;
+            const float ux = (jgx + 0.5f * Fx) * inv_rho;
+            const float uy = (jgy + 0.5f * Fy) * inv_rho;
+            const int t30 = slot3(y);
+            const float mphx = s_m[(t30 * 2) * WM + tid + 1], mphy = s_m[(t30 * 2 + 1) * WM + tid + 1];
+            const float upx = s_u[(t30 * 2) * WM + tid + 1], upy = s_u[(t30 * 2 + 1) * WM + tid + 1];
+            const float mx = rho * ux + mphx, my = rho * uy + mphy;
+            const float ugr = ux * grx + uy * gry;
+            float rho_prev = P.rhoN;
+#pragma unroll
+            for (int p = 0; p < NS; ++p) rho_prev += P.drho[p] * php[p];
+            const float mu_t = mx * ux + my * uy;
+            const float mu_prev = (rho_prev * upx + mpx) * upx + (rho_prev * upy + mpy) * upy;
+            // Eq. (25c): P = c_s^2/(1-w0) [sum_{i!=0} g_i + u.grad rho/2
+            //   - w0 m.u/(2 c_s^2) + w0 d_t(m.u)/(4 c_s^2)], c_s^2 = 1/3, w0 = 4/9
+            const float Pr = 0.6f * (sg + 0.5f * ugr - (2.f / 3.f) * mu_t + (1.f / 3.f) * (mu_t - mu_prev));
+
+            // phase-field collisions, Eqs. (18),(19) in moment space
+            const int s3 = slot3(y), s2 = slot2(y);
+            const float s1 = P.s1, c1 = 1.f - s1, h1 = (1.f - 0.5f * s1) * (1.f / 3.f);
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+                const float phi = ph[p];
+                const float jx = s_j[(s3 * 3 * NS + 3 * p) * TX + tid];
+                const float jy = s_j[(s3 * 3 * NS + 3 * p + 1) * TX + tid];
+                const float plo = s_j[(s3 * 3 * NS + 3 * p + 2) * TX + tid];
+                const float Rx = s_R[(s2 * 2 * NS + 2 * p) * TX + tid];
+                const float Ry = s_R[(s2 * 2 * NS + 2 * p + 1) * TX + tid];
+                // G = d_t(phi u)/c_s^2 + R_p
+                const float Gx = 3.f * (phi * ux - php[p] * upx) + Rx;
+                const float Gy = 3.f * (phi * uy - php[p] * upy) + Ry;
+                const float A = c1 * jx + s1 * phi * ux + h1 * Gx;
+                const float B = c1 * jy + s1 * phi * uy + h1 * Gy;
+                const float C = phi * uy * (1.f / 3.f) + Gy * (1.f / 18.f);
+                const float D = phi * ux * (1.f / 3.f) + Gx * (1.f / 18.f);
+                // f*_i = w_i phi + (moment terms); the four +-pairs around
+                // phi/9 and phi/36 are stored so that each sums exactly to
+                // 2 phi/9 or 2 phi/36, and f*_0 = 4 phi/9 is formed as
+                // (sum_i f_i) - 5 p9 with error-free subtractions, so the
+                // stored populations sum to the pulled ones up to one
+                // rounding (volume conservation, Eq. (1)).
+                const float p9 = phi * (1.f / 9.f), p36 = 0.25f * p9;
+                float f1, f2, f3, f4, f5, f6, f7, f8;
+                exact_pair(p9, 0.5f * (A - D), f1, f3);
+                exact_pair(p9, 0.5f * (B - C), f2, f4);
+                exact_pair(p36, 0.25f * (C + D), f5, f7);
+                exact_pair(p36, 0.25f * (C - D), f6, f8);
+                float e1, e2;
+                const float a1 = two_sum(phi, -4.f * p9, e1);
+                const float a2 = two_sum(a1, -p9, e2);
+                const float f0 = a2 + ((e1 + e2) + plo);
+                float *fo = P.fout + (size_t)p * 9 * pl + node;
+                fo[0 * pl] = f0;
+                fo[1 * pl] = f1;
+                fo[2 * pl] = f2;
+                fo[3 * pl] = f3;
+                fo[4 * pl] = f4;
+                fo[5 * pl] = f5;
+                fo[6 * pl] = f6;
+                fo[7 * pl] = f7;
+                fo[8 * pl] = f8;
+                P.phi[(size_t)p * pl + node] = phi;
+            }
+
+            // flow collision, Eqs. (21)-(24), tau_g from Eq. (26)
+            {
+                const float s2r = 2.f * rho / (6.f * mu + rho);   // 1/tau_g, tau_g = 3 mu/rho + 1/2
+                const float c2 = 1.f - s2r, h2 = 1.f - 0.5f * s2r;
+                const float Qxx = mx * ux, Qyy = my * uy, Qxy = 0.5f * (mx * uy + my * ux);
+                const float dQxx = mphx * ux - mpx * upx;
+                const float dQyy = mphy * uy - mpy * upy;
+                const float dQxy = 0.5f * ((mphx * uy + mphy * ux) - (mpx * upy + mpy * upx));
+                const float Mxx = 2.f * ux * Fx + dQxx + (2.f / 3.f) * ux * grx + (1.f / 3.f) * ugr;
+                const float Myy = 2.f * uy * Fy + dQyy + (2.f / 3.f) * uy * gry + (1.f / 3.f) * ugr;
+                const float Mxy = ux * Fy + Fx * uy + dQxy + (1.f / 3.f) * (ux * gry + grx * uy);
+                const float m1 = jgx + Fx, m2 = jgy + Fy;
+                const float m3 = c2 * Pxx + s2r * (Pr + Qxx) + h2 * Mxx;
+                const float m4 = c2 * Pyy + s2r * (Pr + Qyy) + h2 * Myy;
+                const float m5 = c2 * Pxy + s2r * Qxy + h2 * Mxy;
+                const float m6 = rho * uy * (1.f / 3.f) + Fy * (1.f / 6.f);
+                const float m7 = rho * ux * (1.f / 3.f) + Fx * (1.f / 6.f);
+                const float m8 = (Pr + Qxx + Qyy) * (1.f / 3.f) + (Mxx + Myy) * (1.f / 6.f) - ugr * (1.f / 18.f);
+                float *go = P.gout + node;
+                go[0 * pl] = 0.5f * ((m1 - m7) + (m3 - m8));
+                go[1 * pl] = 0.5f * ((m2 - m6) + (m4 - m8));
+                go[2 * pl] = 0.5f * ((m7 - m1) + (m3 - m8));
+                go[3 * pl] = 0.5f * ((m6 - m2) + (m4 - m8));
+                go[4 * pl] = 0.25f * ((m5 + m6) + (m7 + m8));
+                go[5 * pl] = 0.25f * ((m6 - m5) + (m8 - m7));
+                go[6 * pl] = 0.25f * ((m5 - m6) + (m8 - m7));
+                go[7 * pl] = 0.25f * ((m7 - m5) + (m8 - m6));
+            }
+            P.uout[node] = ux;
+            P.uout[pl + node] = uy;
+            P.mphi[node] = mphx;
+            P.mphi[pl + node] = mphy;
+            if (P.pout) P.pout[node] = Pr;
+        }
+    }
+}
+
+template <int NS, int MODEL>
+cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * ((size_t)5 * NS * (tx + 4) + 12 * (size_t)(tx + 2) +
+                                         (size_t)13 * NS * tx);
+    // The dynamic shared-memory limit is a per-device function attribute.
+    static int configured_bytes[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if ((int)smem > configured_bytes[dev]) {
+        e = cudaFuncSetAttribute(step_kernel<NS, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_bytes[dev] = (int)smem;
+    }
+    dim3 grid((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty);
+    step_kernel<NS, MODEL><<<grid, tx, smem, st>>>(p, ty);
+    return cudaGetLastError();
+}
+
+template <int MODEL>
+cudaError_t launch_step_model(int ns, const StepParams &p, int tx, int ty, cudaStream_t st)
+{
+    switch (ns) {
+    case 1: return launch_step_ns<1, MODEL>(p, tx, ty, st);
+    case 2: return launch_step_ns<2, MODEL>(p, tx, ty, st);
+    case 3: return launch_step_ns<3, MODEL>(p, tx, ty, st);
+    case 4: return launch_step_ns<4, MODEL>(p, tx, ty, st);
+    case 5: return launch_step_ns<5, MODEL>(p, tx, ty, st);
+    case 6: return launch_step_ns<6, MODEL>(p, tx, ty, st);
+    case 7: return launch_step_ns<7, MODEL>(p, tx, ty, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nlbm

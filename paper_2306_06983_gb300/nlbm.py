@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in ``include/nlbm.h`` (argument marshalling
+only: every step of the method runs in the CUDA library ``libnlbm.so``).
+
+PyTorch supplies device memory and streams.  The functions ``nlbm_*`` mirror
+the C entry points one to one; :class:`Simulation` wraps a handle together
+with the workspace tensor that backs it.
+
+The library must have been built (``paper_2306_06983_gb300.build.build()``);
+importing this module does not build it, and loading fails loudly when the
+shared object is missing -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libnlbm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "nlbm.h")
+
+NLBM_OK, NLBM_EINVAL, NLBM_ENOMEM, NLBM_ECUDA, NLBM_ENOTSUP, NLBM_EDIVERGED = range(6)
+NLBM_BC_PERIODIC, NLBM_BC_WALL = 0, 1
+NLBM_MODEL_A, NLBM_MODEL_B = 0, 1
+NLBM_STORE_F32, NLBM_STORE_BF16, NLBM_STORE_F16 = 0, 1, 2
+STATUS_NAMES = {0: "NLBM_OK", 1: "NLBM_EINVAL", 2: "NLBM_ENOMEM", 3: "NLBM_ECUDA",
+                4: "NLBM_ENOTSUP", 5: "NLBM_EDIVERGED"}
+
+
+class NlbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class nlbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("n_phases", ctypes.c_int32), ("model", ctypes.c_int32),
+        ("model_a_n", ctypes.c_double), ("eps", ctypes.c_double), ("mobility", ctypes.c_double),
+        ("rho", ctypes.POINTER(ctypes.c_double)), ("mu", ctypes.POINTER(ctypes.c_double)),
+        ("sigma", ctypes.POINTER(ctypes.c_double)),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnlbm.so and declare every exported signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is not built; run __graft_entry__.build() or "
+            "python -m paper_2306_06983_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, vp, st = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int
+    sig = {
+        "nlbm_workspace_bytes": (st, [P(nlbm_params), P(ctypes.c_size_t)]),
+        "nlbm_create": (st, [P(nlbm_params), vp, ctypes.c_size_t, vp, P(vp)]),
+        "nlbm_set_phi": (st, [vp, vp]),
+        "nlbm_set_phi_host": (st, [vp, vp]),
+        "nlbm_step": (st, [vp, ctypes.c_int64]),
+        "nlbm_get_moments": (st, [vp, vp, vp, vp]),
+        "nlbm_get_moments_host": (st, [vp, vp, vp, vp]),
+        "nlbm_phase_mass": (st, [vp, P(ctypes.c_double)]),
+        "nlbm_state_bytes": (st, [vp, P(ctypes.c_size_t)]),
+        "nlbm_save": (st, [vp, vp]),
+        "nlbm_restore": (st, [vp, vp]),
+        "nlbm_synchronize": (st, [vp]),
+        "nlbm_steps_done": (ctypes.c_int64, [vp]),
+        "nlbm_kernel_launches": (ctypes.c_int64, [vp]),
+        "nlbm_set_tile": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "nlbm_get_tile": (st, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "nlbm_destroy": (None, [vp]),
+        "nlbm_last_error": (ctypes.c_char_p, [vp]),
+        "nlbm_status_string": (ctypes.c_char_p, [st]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions declared in include/nlbm.h."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(nlbm_[a-z_]+)\s*\(", text)))
+
+
+def _check(st: int, handle=None):
+    if st != NLBM_OK:
+        msg = load_library().nlbm_last_error(handle).decode()
+        raise NlbmError(st, msg)
+
+
+def make_params(p: dict):
+    """ctypes parameter block from a workload dict; returns (struct, keepalive)."""
+    N = int(p["n_phases"])
+    rho = (ctypes.c_double * N)(*[float(v) for v in p["rho"]])
+    mu = (ctypes.c_double * N)(*[float(v) for v in p["mu"]])
+    sig = np.asarray(p["sigma"], dtype=np.float64).reshape(N, N)
+    sigma = (ctypes.c_double * (N * N))(*[float(v) for v in sig.ravel()])
+    s = nlbm_params()
+    s.nx, s.ny = int(p["nx"]), int(p["ny"])
+    s.bc_x = NLBM_BC_WALL if p.get("wall_x") else NLBM_BC_PERIODIC
+    s.bc_y = NLBM_BC_WALL if p.get("wall_y") else NLBM_BC_PERIODIC
+    s.n_phases = N
+    s.model = {"A": NLBM_MODEL_A, "B": NLBM_MODEL_B}[p["model"]]
+    s.model_a_n = float(p.get("model_a_n", 1.0))
+    s.eps, s.mobility = float(p["eps"]), float(p["mobility"])
+    s.rho = ctypes.cast(rho, ctypes.POINTER(ctypes.c_double))
+    s.mu = ctypes.cast(mu, ctypes.POINTER(ctypes.c_double))
+    s.sigma = ctypes.cast(sigma, ctypes.POINTER(ctypes.c_double))
+    s.gx = float(p.get("gx", 0.0))
+    s.gy = float(p.get("gy", 0.0))
+    s.storage = int(p.get("storage", NLBM_STORE_F32))
+    s.reserved = 0
+    return s, (rho, mu, sigma)
+
+
+# ------------------------------------------------- one-to-one C entry points
+
+def nlbm_workspace_bytes(params: dict) -> int:
+    s, keep = make_params(params)
+    out = ctypes.c_size_t(0)
+    _check(load_library().nlbm_workspace_bytes(ctypes.byref(s), ctypes.byref(out)))
+    return int(out.value)
+
+
+def nlbm_create(params: dict, workspace_ptr: int, workspace_bytes: int, stream_ptr: int) -> int:
+    s, keep = make_params(params)
+    h = ctypes.c_void_p()
+    _check(load_library().nlbm_create(ctypes.byref(s), ctypes.c_void_p(workspace_ptr),
+                                      workspace_bytes, ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def nlbm_set_phi(h, dev_ptr: int):
+    _check(load_library().nlbm_set_phi(h, ctypes.c_void_p(dev_ptr)), h)
+
+
+def nlbm_set_phi_host(h, host_ptr: int):
+    _check(load_library().nlbm_set_phi_host(h, ctypes.c_void_p(host_ptr)), h)
+
+
+def nlbm_step(h, nsteps: int):
+    _check(load_library().nlbm_step(h, int(nsteps)), h)
+
+
+def nlbm_get_moments(h, phi_ptr=None, u_ptr=None, p_ptr=None):
+    _check(load_library().nlbm_get_moments(h, phi_ptr, u_ptr, p_ptr), h)
+
+
+def nlbm_get_moments_host(h, phi_ptr=None, u_ptr=None, p_ptr=None):
+    _check(load_library().nlbm_get_moments_host(h, phi_ptr, u_ptr, p_ptr), h)
+
+
+def nlbm_phase_mass(h, N: int, allow_diverged: bool = False) -> np.ndarray:
+    out = (ctypes.c_double * N)()
+    st = load_library().nlbm_phase_mass(h, out)
+    if not (allow_diverged and st == NLBM_EDIVERGED):
+        _check(st, h)
+    return np.array(out[:], dtype=np.float64)
+
+
+def nlbm_state_bytes(h) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load_library().nlbm_state_bytes(h, ctypes.byref(out)), h)
+    return int(out.value)
+
+
+def nlbm_save(h, dev_ptr: int):
+    _check(load_library().nlbm_save(h, ctypes.c_void_p(dev_ptr)), h)
+
+
+def nlbm_restore(h, dev_ptr: int):
+    _check(load_library().nlbm_restore(h, ctypes.c_void_p(dev_ptr)), h)
+
+
+def nlbm_synchronize(h):
+    _check(load_library().nlbm_synchronize(h), h)
+
+
+def nlbm_steps_done(h) -> int:
+    return int(load_library().nlbm_steps_done(h))
+
+
+def nlbm_kernel_launches(h) -> int:
+    return int(load_library().nlbm_kernel_launches(h))
+
+
+def nlbm_set_tile(h, tx: int, ty: int):
+    _check(load_library().nlbm_set_tile(h, int(tx), int(ty)), h)
+
+
+def nlbm_get_tile(h):
+    tx, ty = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().nlbm_get_tile(h, ctypes.byref(tx), ctypes.byref(ty)), h)
+    return tx.value, ty.value
+
+
+def nlbm_destroy(h):
+    load_library().nlbm_destroy(h)
+
+
+def nlbm_last_error(h=None) -> str:
+    return load_library().nlbm_last_error(h).decode()
+
+
+def nlbm_status_string(st: int) -> str:
+    return load_library().nlbm_status_string(st).decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class Simulation:
+    """One simulation on the current CUDA device; the workspace is a torch
+    uint8 tensor owned by this object."""
+
+    def __init__(self, params: dict, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.params = dict(params)
+        self.N = int(params["n_phases"])
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = nlbm_workspace_bytes(params)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.h = ctypes.c_void_p(nlbm_create(params, aligned, nbytes, self.stream.cuda_stream))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            nlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state
+    def set_phi(self, phi0):
+        """phi0: [N-1, ny, nx] numpy array or CUDA tensor (phases 1..N-1)."""
+        torch = self.torch
+        t = torch.as_tensor(phi0)
+        if t.shape != (self.N - 1, self.ny, self.nx):
+            raise ValueError(f"phi0 has shape {tuple(t.shape)}, expected {(self.N - 1, self.ny, self.nx)}")
+        t = t.to(device=self.device, dtype=torch.float32).contiguous()
+        self._phi0 = t
+        nlbm_set_phi(self.h, t.data_ptr())
+
+    def set_phi_host(self, phi0_host):
+        """phi0_host: float32 CPU tensor (pinned or pageable) [N-1, ny, nx]."""
+        t = self.torch.as_tensor(phi0_host)
+        assert t.device.type == "cpu" and t.dtype == self.torch.float32 and t.is_contiguous()
+        assert t.shape == (self.N - 1, self.ny, self.nx)
+        nlbm_set_phi_host(self.h, t.data_ptr())
+
+    def step(self, n: int):
+        nlbm_step(self.h, n)
+
+    def moments(self):
+        """(phi [N,ny,nx], u [2,ny,nx], P [ny,nx]) as new CUDA tensors."""
+        torch = self.torch
+        phi = torch.empty((self.N, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        P = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
+        nlbm_get_moments(self.h, phi.data_ptr(), u.data_ptr(), P.data_ptr())
+        return phi, u, P
+
+    def moments_host(self, phi=None, u=None, P=None):
+        """Fill CPU float32 tensors (allocated if None) through the host entry point."""
+        torch = self.torch
+        if phi is None:
+            phi = torch.empty((self.N, self.ny, self.nx), dtype=torch.float32)
+        if u is None:
+            u = torch.empty((2, self.ny, self.nx), dtype=torch.float32)
+        if P is None:
+            P = torch.empty((self.ny, self.nx), dtype=torch.float32)
+        nlbm_get_moments_host(self.h, phi.data_ptr(), u.data_ptr(), P.data_ptr())
+        return phi, u, P
+
+    def phase_mass(self, allow_diverged: bool = False) -> np.ndarray:
+        return nlbm_phase_mass(self.h, self.N, allow_diverged)
+
+    def save(self):
+        n = nlbm_state_bytes(self.h)
+        buf = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        nlbm_save(self.h, buf.data_ptr())
+        return buf
+
+    def restore(self, buf):
+        nlbm_restore(self.h, buf.data_ptr())
+
+    def synchronize(self):
+        nlbm_synchronize(self.h)
+
+    @property
+    def steps_done(self) -> int:
+        return nlbm_steps_done(self.h)
+
+    @property
+    def kernel_launches(self) -> int:
+        return nlbm_kernel_launches(self.h)
+
+    def set_tile(self, tx: int, ty: int):
+        nlbm_set_tile(self.h, tx, ty)
+
+    def get_tile(self):
+        return nlbm_get_tile(self.h)

@@ -43,6 +43,26 @@ def disk(nx: int, ny: int, cx: float, cy: float, R: float, eps: float,
     return 0.5 + 0.5 * np.tanh((R - r) / (eps / 2.0))
 
 
+def _add_disk_windowed(field: np.ndarray, cx: float, cy: float, R: float, eps: float) -> None:
+    """Add a periodic tanh disk (Eq. (30) profile) inside the window of
+    half-width R + 10 eps around its centre; outside it the profile is below
+    1e-17 and is taken as exactly 0."""
+    ny, nx = field.shape
+    h = R + 10.0 * eps
+    xs = np.arange(int(np.floor(cx - h)), int(np.ceil(cx + h)) + 1)
+    ys = np.arange(int(np.floor(cy - h)), int(np.ceil(cy + h)) + 1)
+    if len(xs) >= nx:
+        xs = np.arange(nx)
+    if len(ys) >= ny:
+        ys = np.arange(ny)
+    dx = _axis_dist(xs.astype(np.float64), cx, nx, True)[None, :]
+    dy = _axis_dist(ys.astype(np.float64), cy, ny, True)[:, None]
+    r = np.sqrt(dx * dx + dy * dy)
+    val = 0.5 + 0.5 * np.tanh((R - r) / (eps / 2.0))
+    val[r > h] = 0.0
+    field[np.ix_(ys % ny, xs % nx)] += val
+
+
 def flat_band(nx: int, ny: int, y0: float, y1: float, eps: float) -> np.ndarray:
     """Band y0 < y < y1 (periodic in y) with the equilibrium profile
     0.5 + 0.5 tanh(2 d / eps) of Sec. 2.1, d the signed distance to the
@@ -120,7 +140,7 @@ def random_disks(nx, ny, N, n_disks, rmin, rmax, seed=SEED, model="B", model_a_n
         raise RuntimeError(f"placed only {len(disks)} of {n_disks} disks")
     fields = np.zeros((N + 1, ny, nx))
     for (cx, cy, R, lab) in disks:
-        fields[lab] += disk(nx, ny, cx, cy, R, eps)
+        _add_disk_windowed(fields[lab], cx, cy, R, eps)
     phi = np.empty((N, ny, nx))
     phi[0] = 1.0 - fields[2:N + 1].sum(axis=0)
     for lab in range(2, N + 1):

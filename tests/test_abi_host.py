@@ -1,0 +1,117 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/nlbm.h declares, and validates the
+problem statement (no compute call is made here)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2306_06983_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_06983_gb300.build import build
+    from paper_2306_06983_gb300 import nlbm
+    build()
+    return nlbm.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2306_06983_gb300 import nlbm
+    names = nlbm.declared_symbols()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+        assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
+
+
+def test_status_strings(lib):
+    from paper_2306_06983_gb300 import nlbm
+    assert nlbm.nlbm_status_string(0) == "ok"
+    assert nlbm.nlbm_status_string(5) == "diverged"
+
+
+def test_workspace_bytes_scales_with_lattice(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    b64 = nlbm.nlbm_workspace_bytes(p)
+    b128 = nlbm.nlbm_workspace_bytes(dict(p, nx=128, ny=128))
+    # 2x(9(N-1)+8) + (N-1) + 2x2 + 2 + 1 planes of float32
+    planes = 2 * (9 * 2 + 8) + 2 + 4 + 2 + 1
+    assert b64 >= planes * 64 * 64 * 4
+    assert abs(b128 / b64 - 4.0) < 0.05
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (dict(n_phases=1), 1), (dict(n_phases=9), 1), (dict(nx=0), 1), (dict(eps=0.0), 1),
+    (dict(eps=float("nan")), 1), (dict(mobility=-0.1), 1), (dict(model="A", model_a_n=0.0), 1),
+    (dict(gx=1e-5), 4), (dict(storage=1), 4), (dict(storage=7), 1),
+    (dict(wall_y=True, ny=3), 1),
+])
+def test_parameter_validation(lib, mutate, status):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    q = dict(p)
+    N = int(mutate.get("n_phases", q["n_phases"]))
+    if N != q["n_phases"]:
+        q["rho"] = [1.0] * max(N, 1)
+        q["mu"] = [0.1] * max(N, 1)
+        q["sigma"] = (np.full((max(N, 1), max(N, 1)), 0.01) * (1 - np.eye(max(N, 1)))).tolist()
+    q.update(mutate)
+    with pytest.raises(nlbm.NlbmError) as ei:
+        nlbm.nlbm_workspace_bytes(q)
+    assert ei.value.status == status
+
+
+def test_sigma_must_be_symmetric_positive(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    s = np.array(p["sigma"])
+    s[0, 1] = 0.02
+    with pytest.raises(nlbm.NlbmError):
+        nlbm.nlbm_workspace_bytes(dict(p, sigma=s.tolist()))
+    s = np.array(p["sigma"])
+    s[1, 1] = 0.01
+    with pytest.raises(nlbm.NlbmError):
+        nlbm.nlbm_workspace_bytes(dict(p, sigma=s.tolist()))
+    with pytest.raises(nlbm.NlbmError):
+        nlbm.nlbm_workspace_bytes(dict(p, rho=[1.0, -1.0, 1.0]))
+
+
+def test_create_rejects_bad_workspace(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    n = nlbm.nlbm_workspace_bytes(p)
+    with pytest.raises(nlbm.NlbmError) as ei:
+        nlbm.nlbm_create(p, 0, n, 0)
+    assert ei.value.status == nlbm.NLBM_EINVAL
+    with pytest.raises(nlbm.NlbmError) as ei:
+        nlbm.nlbm_create(p, 4096 + 16, n, 0)      # unaligned (never dereferenced)
+    assert ei.value.status == nlbm.NLBM_EINVAL
+    with pytest.raises(nlbm.NlbmError) as ei:
+        nlbm.nlbm_create(p, 4096, n - 256, 0)     # too small (never dereferenced)
+    assert ei.value.status == nlbm.NLBM_ENOMEM
+
+
+def test_tile_validation(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    n = nlbm.nlbm_workspace_bytes(p)
+    # a handle over a fake (never dereferenced) aligned address: only host
+    # bookkeeping calls are made on it
+    h = ctypes.c_void_p(nlbm.nlbm_create(p, 1 << 20, n, 0))
+    try:
+        assert nlbm.nlbm_get_tile(h) == (64, 32)
+        nlbm.nlbm_set_tile(h, 128, 16)
+        assert nlbm.nlbm_get_tile(h) == (128, 16)
+        for tx, ty in [(16, 8), (48, 8), (512, 8), (64, 0)]:
+            with pytest.raises(nlbm.NlbmError):
+                nlbm.nlbm_set_tile(h, tx, ty)
+        assert nlbm.nlbm_steps_done(h) == 0
+        assert nlbm.nlbm_kernel_launches(h) == 0
+        nlbm.nlbm_step(h, 0)                      # zero steps launch nothing
+        assert nlbm.nlbm_kernel_launches(h) == 0
+    finally:
+        nlbm.nlbm_destroy(h)

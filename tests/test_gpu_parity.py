@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances.  The library computes in FP32.  How far FP32 rounding alone
+moves this method is measured, not guessed: the oracle's own source built in
+FP32 (a noise model, never a reference) is run beside the FP64 oracle, and
+the GPU must stay within a small multiple K of that spread (plus a floor).
+The method amplifies rounding where a phase field overshoots 1 in a drop's
+bulk (R = a n with a != 0 follows a near-zero gradient), so the spread grows
+from ~3e-7 after one step to 1e-5..1e-3 after ten on droplet problems;
+element-wise checks therefore use 1 and 3 steps, where u and P remain
+sensitive to any wrong term, and long runs are judged by the FP64
+mass drift (<= 1e-6) and the FP32 spread."""
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim
+from paper_2306_06983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_2306_06983_gb300.build import build
+    from oracle.oracle import build_oracle
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build()
+    build_oracle()
+    torch.cuda.set_device(0)
+
+
+def gpu_run(p, phi0, steps, tile=None):
+    from paper_2306_06983_gb300.nlbm import Simulation
+    sim = Simulation(p)
+    if tile:
+        sim.set_tile(*tile)
+    sim.set_phi(phi0)
+    m0 = sim.phase_mass()
+    out = []
+    done = 0
+    for s in (steps if isinstance(steps, (list, tuple)) else [steps]):
+        sim.step(s - done)
+        done = s
+        phi, u, P = (t.cpu().numpy().astype(np.float64) for t in sim.moments())
+        out.append((phi, u, P, sim.phase_mass()))
+    sim.close()
+    return m0, out
+
+
+def oracle_run(p, phi0, steps):
+    o = OracleSim(p, phi0)
+    out = []
+    done = 0
+    for s in (steps if isinstance(steps, (list, tuple)) else [steps]):
+        o.step(s - done)
+        done = s
+        out.append(o.moments())
+    return out
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+CASES = {
+    "droplets64_B": lambda: W.droplets_64("B"),
+    "droplets64_A1": lambda: W.droplets_64("A", 1.0),
+    "droplets64_A2": lambda: W.droplets_64("A", 2.0),
+    "disks256_B": lambda: W.disks_256("B"),
+    "disks256_A2": lambda: W.disks_256("A", 2.0),
+    "ragged67x45_N4_B": lambda: W.random_smooth(67, 45, 4, seed=3, model="B"),
+    "ragged67x45_N4_A_walls": lambda: W.random_smooth(67, 45, 4, seed=4, model="A", model_a_n=1.5,
+                                                      wall_x=True, wall_y=True),
+    "ragged45x67_N2_B_wally": lambda: W.random_smooth(45, 67, 2, seed=5, model="B", wall_y=True),
+    "ragged130x33_N8_B_wallx": lambda: W.random_smooth(130, 33, 8, seed=6, model="B", wall_x=True),
+    "ragged200x71_N6_A3": lambda: W.random_smooth(200, 71, 6, seed=7, model="A", model_a_n=3.0),
+    "tiny5x7_N3_B": lambda: W.random_smooth(5, 7, 3, seed=8, model="B", n_disks=1),
+    "tiny8x8_N7_A": lambda: W.random_smooth(8, 8, 7, seed=9, model="A", n_disks=3),
+    "tiny4x4_N2_B_walls": lambda: W.random_smooth(4, 4, 2, seed=10, model="B", wall_x=True,
+                                                  wall_y=True, n_disks=1),
+    "line1x9_N3_B": lambda: W.random_smooth(1, 9, 3, seed=11, model="B", n_disks=1),
+}
+
+
+def fp32_spread(p, phi0, steps):
+    """Per checkpoint: max |phi|, |u|, |P| differences between the FP32
+    noise-model build and the FP64 oracle, plus the FP64 moments."""
+    a, b = OracleSim(p, phi0), OracleSim(p, phi0, fp32=True)
+    out = []
+    for s in steps:
+        a.step(s - a.steps_done)
+        b.step(s - b.steps_done)
+        A, B = a.moments(), b.moments()
+        out.append((A, [np.abs(x - y).max() for x, y in zip(A, B)],
+                    np.abs(A[0] - B[0]).mean()))
+    return out
+
+
+K = 4.0
+FLOORS = (2e-6, 1e-8, 1e-8)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_short_horizon_parity(case):
+    p, phi0 = CASES[case]()
+    phi0 = f32(phi0)
+    steps = [1, 3]
+    m0, g = gpu_run(p, phi0, steps)
+    ref = fp32_spread(p, phi0, steps)
+    for s, (gphi, gu, gP, _), (orc, spread, _) in zip(steps, g, ref):
+        for name, gv, ov, sp, fl in zip(("phi", "u", "P"), (gphi, gu, gP), orc, spread, FLOORS):
+            err = np.abs(gv - ov).max()
+            tol = max(fl, K * sp)
+            assert err <= tol, (case, s, name, err, tol)
+    mass = g[-1][3]
+    scale = p["nx"] * p["ny"]
+    assert np.abs(mass - m0).max() / scale < 1e-7
+
+
+@pytest.mark.parametrize("case", ["droplets64_B", "droplets64_A2", "disks256_B", "ragged45x67_N2_B_wally"])
+def test_ten_step_parity(case):
+    """Ten steps, element-wise, where the FP32 spread is still small."""
+    p, phi0 = CASES[case]()
+    phi0 = f32(phi0)
+    _, g = gpu_run(p, phi0, 10)
+    (orc, spread, _), = fp32_spread(p, phi0, [10])
+    for name, gv, ov, sp, fl in zip(("phi", "u", "P"), g[0][:3], orc, spread, FLOORS):
+        err = np.abs(gv - ov).max()
+        assert err <= max(fl, K * sp), (case, name, err, sp)
+
+
+@pytest.mark.parametrize("model,n", [("B", 1.0), ("A", 1.0), ("A", 2.0)])
+def test_droplets64_2000_steps(model, n):
+    """64x64, N = 3, 2000 steps: per-phase mass drift <= 1e-6 relative
+    (FP64-accumulated); max and mean |d phi| and max |d u| within 3x the FP32
+    spread of the oracle's own algorithm."""
+    p, phi0 = W.droplets_64(model, n)
+    phi0r = f32(phi0)
+    m0, g = gpu_run(p, phi0r, 2000)
+    gphi, gu, gP, m1 = g[0]
+    ((ophi, ou, oP), spread, mean_spread), = fp32_spread(p, phi0r, [2000])
+    d = np.abs(gphi - ophi)
+    drift = np.abs(m1 - m0) / m0
+    print(f"\n{model}{n}: max|dphi| {d.max():.3e} (fp32 spread {spread[0]:.3e}) mean {d.mean():.3e} "
+          f"(spread {mean_spread:.3e}) max|du| {np.abs(gu - ou).max():.3e} "
+          f"(spread {spread[1]:.3e}) drift {drift.max():.3e}")
+    assert np.all(drift <= 1e-6), drift
+    assert d.max() <= max(1e-5, 3 * spread[0])
+    assert d.mean() <= max(1e-6, 3 * mean_spread)
+    assert np.abs(gu - ou).max() <= max(1e-8, 3 * spread[1])
+
+
+def test_flat_band_2000_steps():
+    """A flat interface over 2000 steps: within 3x the FP32 spread."""
+    nx, ny = 16, 64
+    p = W.base_params(nx, ny, 2, model="B", sigma=0.01)
+    b = f32(W.flat_band(nx, ny, 16, 48, 4.0))[None]
+    m0, g = gpu_run(p, b, 2000)
+    ((ophi, ou, oP), spread, _), = fp32_spread(p, b, [2000])
+    assert np.abs(g[0][0] - ophi).max() <= max(1e-6, 3 * spread[0])
+    assert np.abs(g[0][1] - ou).max() <= max(1e-8, 3 * spread[1])
+    assert np.all(np.abs(g[0][3] - m0) / m0 <= 1e-6)
+
+
+def test_reduction_consistency_gpu():
+    """An absent phase stays exactly absent on the GPU and the three-phase run
+    reproduces the two-phase run."""
+    nx, ny = 48, 40
+    d = f32(W.disk(nx, ny, 20.3, 17.6, 9, 4.0))
+    p3 = W.base_params(nx, ny, 3, model="B", rho=[1.0, 7.0, 3.0], mu=[0.2, 0.9, 0.1],
+                       sigma=[[0, 0.013, 0.01], [0.013, 0, 0.017], [0.01, 0.017, 0]])
+    p2 = W.base_params(nx, ny, 2, model="B", rho=[1.0, 3.0], mu=[0.2, 0.1],
+                       sigma=[[0, 0.01], [0.01, 0]])
+    _, g3 = gpu_run(p3, np.stack([d, np.zeros_like(d)]), 300)
+    _, g2 = gpu_run(p2, d[None], 300)
+    assert np.all(g3[0][0][1] == 0.0)
+    np.testing.assert_allclose(g3[0][0][0], g2[0][0][0], atol=1e-6)
+    np.testing.assert_allclose(g3[0][1], g2[0][1], atol=1e-8)
+
+
+@pytest.mark.parametrize("tile", [(32, 1), (32, 7), (64, 32), (128, 16), (256, 64), (96, 5)])
+def test_tile_invariance(tile):
+    """The decomposition into column strips and row chunks does not change the
+    result: every node is computed by the same code from the same inputs."""
+    p, phi0 = W.random_smooth(200, 71, 5, seed=12, model="B", wall_y=True)
+    phi0 = f32(phi0)
+    _, ref = gpu_run(p, phi0, 25, tile=(64, 32))
+    _, got = gpu_run(p, phi0, 25, tile=tile)
+    np.testing.assert_allclose(got[0][0], ref[0][0], atol=1e-6, rtol=0)
+    np.testing.assert_allclose(got[0][1], ref[0][1], atol=1e-9, rtol=0)
+
+
+def test_transpose_symmetry_gpu():
+    """A transposed initial state gives the transposed state with u_x, u_y
+    swapped (3 steps, within the FP32 spread)."""
+    p, phi0 = W.random_smooth(48, 48, 4, seed=13, model="A", model_a_n=2.0)
+    phi0 = f32(phi0)
+    _, a = gpu_run(p, phi0, 3)
+    _, b = gpu_run(p, np.ascontiguousarray(phi0.transpose(0, 2, 1)), 3)
+    (_, spread, _), = fp32_spread(p, phi0, [3])
+    np.testing.assert_allclose(b[0][0], a[0][0].transpose(0, 2, 1), atol=max(2e-6, 2 * K * spread[0]))
+    np.testing.assert_allclose(b[0][1][0], a[0][1][1].T, atol=max(1e-8, 2 * K * spread[1]))
+    np.testing.assert_allclose(b[0][1][1], a[0][1][0].T, atol=max(1e-8, 2 * K * spread[1]))
+
+
+def test_checkpoint_restore_bitwise():
+    import torch
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.random_smooth(70, 50, 4, seed=14, model="B")
+    sim = Simulation(p)
+    sim.set_phi(f32(phi0))
+    sim.step(20)
+    ck = sim.save()
+    sim.step(30)
+    a = [t.clone() for t in sim.moments()]
+    sim.restore(ck)
+    assert sim.steps_done == 20
+    sim.step(30)
+    b = sim.moments()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    sim.close()
+
+
+def test_host_entry_points_match_device():
+    import torch
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.random_smooth(61, 37, 3, seed=15, model="B")
+    phi0 = f32(phi0)
+    a = Simulation(p)
+    a.set_phi(phi0)
+    a.step(7)
+    da = [t.cpu() for t in a.moments()]
+    b = Simulation(p)
+    b.set_phi_host(torch.from_numpy(phi0.astype(np.float32)).pin_memory())
+    b.step(7)
+    hb = b.moments_host()
+    for x, y in zip(da, hb):
+        assert torch.equal(x, y)
+    np.testing.assert_allclose(hb[0].sum(0).numpy(), 1.0, atol=1e-6)
+
+
+def test_phase_mass_reproducible_and_exact():
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.disks_256("B")
+    sim = Simulation(p)
+    sim.set_phi(f32(phi0))
+    sim.step(5)
+    m1, m2 = sim.phase_mass(), sim.phase_mass()
+    assert np.array_equal(m1, m2)
+    phi = sim.moments()[0].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(m1[:-1], phi[:-1].reshape(4, -1).sum(1), rtol=1e-12)
+    assert abs(m1.sum() - p["nx"] * p["ny"]) < 1e-6 * p["nx"] * p["ny"]
+
+
+def test_divergence_is_reported():
+    """A non-finite initial value is reported by the mass check (host-made
+    fault; no GPU fault involved)."""
+    from paper_2306_06983_gb300.nlbm import NLBM_EDIVERGED, NlbmError, Simulation
+    p, phi0 = W.droplets_64("B")
+    phi0 = f32(phi0)
+    phi0[0, 5, 5] = np.nan
+    sim = Simulation(p)
+    sim.set_phi(phi0)
+    with pytest.raises(NlbmError) as ei:
+        sim.phase_mass()
+    assert ei.value.status == NLBM_EDIVERGED
+    m = sim.phase_mass(allow_diverged=True)
+    assert np.isnan(m).any()
+
+
+def test_launch_count():
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.droplets_64("B")
+    sim = Simulation(p)
+    sim.set_phi(f32(phi0))
+    n0 = sim.kernel_launches
+    sim.step(17)
+    assert sim.kernel_launches - n0 == 17
+
+
+def test_full_size_disks_2048():
+    """The 2048x2048 five-phase suspension in the launch configuration the
+    benchmark times: 2 steps element-wise against the oracle on sampled rows,
+    then 200 steps of invariants (mass drift, boundedness, no divergence)."""
+    p, phi0 = W.disks_2048("B")
+    phi0 = f32(phi0)
+    m0, g = gpu_run(p, phi0, [2, 200])
+    (ophi, ou, oP), = oracle_run(p, phi0, 2)
+    gphi, gu, gP, _ = g[0]
+    rows = np.random.default_rng(0).choice(p["ny"], 64, replace=False)
+    assert np.abs(gphi[:, rows] - ophi[:, rows]).max() < 2e-6
+    assert np.abs(gu[:, rows] - ou[:, rows]).max() < 1e-7
+    assert np.abs(gP[rows] - oP[rows]).max() < 1e-7
+    phi200, u200, _, m200 = g[1]
+    assert np.all(np.abs(m200 - m0) / np.abs(m0) < 1e-6)
+    assert np.isfinite(phi200).all() and phi200.min() > -0.05 and phi200.max() < 1.05
+    assert np.abs(u200).max() < 0.05
