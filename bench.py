@@ -71,6 +71,25 @@ def measured_traffic(model: str):
         return None
 
 
+def reduce_max_over_ranks(values):
+    """Max over ranks of a list of floats (identity without a process group).
+    Uses the process group's own backend: gloo on CPU tensors, NCCL on CUDA."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_mlups(world: int, lups_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each advancing lups_per_step
+    lattice updates per step, over the slowest rank's time."""
+    return world * lups_per_step * steps / seconds / 1e6
+
+
 def peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -264,16 +283,13 @@ def run_gpu(args):
         sim2.close()
 
     total_s = total_ms / 1e3
-    if world > 1:
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+    total_s, e2e_s = reduce_max_over_ranks([total_s, e2e_s])
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    mlups = world * lups * args.steps / total_s / 1e6
+    mlups = whole_job_mlups(world, lups, args.steps, total_s)
     avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
     bpl = bytes_per_lup(N)
     achieved = bpl * lups / avg_launch_s / 1e9
@@ -296,7 +312,7 @@ def run_gpu(args):
                      "algorithmic_bytes_per_lup": bpl,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "avg_launch_ms": round(avg_launch_s * 1e3, 5)},
-        "e2e": {"value": round(world * lups * args.steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+        "e2e": {"value": round(whole_job_mlups(world, lups, args.steps, e2e_s), 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(4 * (N - 1) * lups / args.steps),
                 "d2h_bytes_per_step": round((4 * (N + 3) * lups + 8 * N) / args.steps),
                 "seconds": round(e2e_s, 4), "gpu_launches": e2e_launches,
