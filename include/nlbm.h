@@ -158,6 +158,35 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s);
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
 nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
 
+/* Per-phase volume sum_x phi_p, p = 1..N, for callers that cannot allocate
+ * device memory at all -- neither through this library's workspace nor their
+ * own allocator: code that runs where cudaMalloc is forbidden or unsafe (a
+ * real-time loop with a fixed memory budget, a plugin handed only the
+ * pointers it computes on, a host callback).  The paper has no counterpart;
+ * it is the reduction of nlbm_phase_mass() with its scratch moved into the
+ * library.
+ *   dev_phi  [n_phases-1][n_nodes] float, phases 1..N-1 (phase N = 1 - sum),
+ *            e.g. the first N-1 planes written by nlbm_get_moments();
+ *   dev_mass [n_phases] double, written: the volumes, FP64-accumulated in a
+ *            fixed order (bitwise equal to nlbm_phase_mass() on the same
+ *            fields);
+ *   dev_flag [1] int32, written: 1 if any value is non-finite or outside
+ *            [-0.5, 1.5], else 0.
+ * The reduction's FP64 partial sums live in one file-scope device array of
+ * 512 x 9 doubles (36.9 KB) that every GPU which loads the library keeps
+ * until the process exits; the call allocates nothing and never calls
+ * cudaMalloc or cudaFree.  n_phases must be 2..8 and n_nodes 1..2^28;
+ * larger sizes are rejected with NLBM_EINVAL (and one line on stderr)
+ * before any GPU work.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make it
+ * before any stream capture.  All calls share the array: every entry the
+ * reduction reads it has first written in the same call, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams, other host
+ * threads) race on it -- serialise them.  Asynchronous on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream). */
+nlbm_status nlbm_phase_mass_noalloc(const float *dev_phi, int32_t n_phases, int64_t n_nodes,
+                                    double *dev_mass, int32_t *dev_flag, void *cuda_stream);
+
 /* Release the handle (not the workspace).  Safe on NULL.  Does not wait for
  * enqueued work; synchronize first if the workspace is to be reused. */
 void nlbm_destroy(nlbm_sim *s);

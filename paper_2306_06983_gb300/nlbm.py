@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "nlbm_destroy": (None, [vp]),
         "nlbm_last_error": (ctypes.c_char_p, [vp]),
         "nlbm_status_string": (ctypes.c_char_p, [st]),
+        "nlbm_phase_mass_noalloc": (st, [vp, ctypes.c_int32, ctypes.c_int64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +222,15 @@ def nlbm_last_error(h=None) -> str:
 
 def nlbm_status_string(st: int) -> str:
     return load_library().nlbm_status_string(st).decode()
+
+
+def nlbm_phase_mass_noalloc(dev_phi: int, n_phases: int, n_nodes: int, dev_mass: int,
+                            dev_flag: int, stream_ptr: int = 0) -> int:
+    """Volume reduction that allocates nothing (scratch is a fixed array
+    inside the library); returns the status code (0 = OK)."""
+    return int(load_library().nlbm_phase_mass_noalloc(
+        ctypes.c_void_p(dev_phi), int(n_phases), int(n_nodes), ctypes.c_void_p(dev_mass),
+        ctypes.c_void_p(dev_flag), ctypes.c_void_p(stream_ptr)))
 
 
 # ------------------------------------------------------------ convenience
