@@ -163,7 +163,7 @@ void default_tile(nlbm_sim *s)
     int tx = 128;
     while (tx > 32 && tx / 2 >= s->kp.nx) tx /= 2;
     s->tx = tx;
-    s->ty = 32;
+    s->ty = 0;
 }
 
 // Number of state bytes in a checkpoint, excluding the trailing counter.
@@ -268,9 +268,7 @@ nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
 nlbm_status nlbm_step(nlbm_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return NLBM_EINVAL;
-    int ty = s->ty;
-    const int min_ty = (s->kp.ny + 65534) / 65535;   // grid.y limit
-    if (ty < min_ty) ty = min_ty;
+    const int ty = s->ty;   // 0: chosen by the launcher
     for (int64_t k = 0; k < nsteps; ++k) {
         StepParams kp = s->kp;
         const int a = s->cur, b = s->cur ^ 1;
@@ -423,8 +421,8 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s) { return s ? s->launches : -1; }
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty)
 {
     if (!s) return NLBM_EINVAL;
-    if (tx < 32 || tx > 256 || tx % 32 != 0 || ty < 1) {
-        set_err(s->err, "tile %dx%d outside tx in {32..256, multiple of 32}, ty >= 1", tx, ty);
+    if (tx < 32 || tx > 256 || tx % 32 != 0 || ty < 0) {
+        set_err(s->err, "tile %dx%d outside tx in {32..256, multiple of 32}, ty >= 0", tx, ty);
         return NLBM_EINVAL;
     }
     s->tx = tx;

@@ -87,14 +87,24 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e)
     return s;
 }
 
-// Pulled phase fields at one node.  phi = f_0 + f_1 + ... + f_8 is summed in
-// this fixed order everywhere (own and halo nodes give identical bits).  For
-// the strip's own nodes the rounding error of that sum (phi_lo, exact when
-// the running sum dominates each term, as the rest population does) and the
-// first moments j_p are returned as well.
-template <int NS, bool OWN>
-__device__ __forceinline__ void pull_phi(const StepParams &P, int x, int y, float (&ph)[NS],
-                                         float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
+// Asynchronous 4-byte global->shared copies (cp.async): the next row's
+// pulled populations are in flight while the current rows are computed.
+__device__ __forceinline__ void cp_async4(float *dst_smem, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one()
+{
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// Start the copies of the 9 (N-1) populations node (x, y) pulls into column
+// col of the staging array s_F [9 (N-1)][WF].
+template <int NS>
+__device__ __forceinline__ void prefetch_pull(const StepParams &P, int x, int y, float *s_F, int WF,
+                                              int col)
 {
     unsigned node[9];
     int dir[9];
@@ -102,10 +112,26 @@ __device__ __forceinline__ void pull_phi(const StepParams &P, int x, int y, floa
     const unsigned pl = P.plane;
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-        const float *__restrict__ fp = P.fin + (size_t)p * 9 * pl;
+        const float *fp = P.fin + (size_t)p * 9 * pl;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cp_async4(s_F + (p * 9 + i) * WF + col, fp + (unsigned)dir[i] * pl + node[i]);
+    }
+}
+
+// Phase fields of one node from its staged pulled populations.  phi = f_0 +
+// f_1 + ... + f_8 is summed in this fixed order everywhere (own and halo
+// nodes give identical bits).  For the strip's own nodes the rounding error
+// of that sum (phi_lo, exact when the running sum dominates each term, as the
+// rest population does) and the first moments j_p are returned as well.
+template <int NS, bool OWN>
+__device__ __forceinline__ void sum_pulled(const float *s_F, int WF, int col, float (&ph)[NS],
+                                           float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
+{
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
         float f[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = __ldg(fp + (unsigned)dir[i] * pl + node[i]);
+        for (int i = 0; i < 9; ++i) f[i] = s_F[(p * 9 + i) * WF + col];
         float s = f[0], e = 0.f;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -168,23 +194,36 @@ __device__ __forceinline__ void window_grad(const float *s_phi, int W, int sm, i
     gy[NS] = -sgy;
 }
 
-// Laplacians (Eq. (27)) of the solved phases from the ring; phase N by -sum.
+// phi, grad phi and lap phi (Eq. (27)) of all N phases from one read of the
+// 3x3 window (phase N by phi_N = 1 - sum and negated sums).
 template <int NS>
-__device__ __forceinline__ void window_lap(const float *s_phi, int W, int sm, int s0, int sp, int c,
-                                           float (&lap)[NS + 1])
+__device__ __forceinline__ void window_grad_lap(const float *s_phi, int W, int sm, int s0, int sp,
+                                                int c, float (&ph)[NS + 1], float (&gx)[NS + 1],
+                                                float (&gy)[NS + 1], float (&lap)[NS + 1])
 {
-    float sl = 0.f;
+    float sph = 0.f, sgx = 0.f, sgy = 0.f, sl = 0.f;
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
         const float *rm = s_phi + (sm * NS + p) * W + c;
         const float *r0 = s_phi + (s0 * NS + p) * W + c;
         const float *rp = s_phi + (sp * NS + p) * W + c;
-        const float ce = r0[0];
-        const float ax = ((r0[1] - ce) + (r0[-1] - ce)) + ((rp[0] - ce) + (rm[0] - ce));
-        const float dg = ((rp[1] - ce) + (rp[-1] - ce)) + ((rm[1] - ce) + (rm[-1] - ce));
+        const float sw = rm[-1], s = rm[0], se = rm[1];
+        const float w = r0[-1], ce = r0[0], e = r0[1];
+        const float nw = rp[-1], n = rp[0], ne = rp[1];
+        ph[p] = ce;
+        gx[p] = (e - w) * (1.f / 3.f) + ((ne + se) - (nw + sw)) * (1.f / 12.f);
+        gy[p] = (n - s) * (1.f / 3.f) + ((ne + nw) - (se + sw)) * (1.f / 12.f);
+        const float ax = ((e - ce) + (w - ce)) + ((n - ce) + (s - ce));
+        const float dg = ((ne - ce) + (nw - ce)) + ((se - ce) + (sw - ce));
         lap[p] = ax * (2.f / 3.f) + dg * (1.f / 6.f);
+        sph += ce;
+        sgx += gx[p];
+        sgy += gy[p];
         sl += lap[p];
     }
+    ph[NS] = 1.f - sph;
+    gx[NS] = -sgx;
+    gy[NS] = -sgy;
     lap[NS] = -sl;
 }
 
@@ -272,11 +311,14 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
     extern __shared__ float smem[];
     const int TX = blockDim.x;
     const int WP = TX + 4, WM = TX + 2;
+    const int WF = TX + 4;                   // staging columns: own nodes, then 4 halo nodes
     float *s_phi = smem;                     // [5][NS][WP]  phi(t) rows r-2..r+2
     float *s_m = s_phi + 5 * NS * WP;        // [3][2][WM]   m_phi(t) rows r-1..r+1
     float *s_u = s_m + 6 * WM;               // [3][2][WM]   u(t-1)   rows r-1..r+1
     float *s_j = s_u + 6 * WM;               // [3][3NS][TX] j_x, j_y, phi_lo of own nodes
     float *s_R = s_j + 9 * NS * TX;          // [2][2NS][TX] sources of own nodes
+    float *s_F = s_R + 4 * NS * TX;          // [9NS][WF]    staged pulled f of the next row
+    float *s_G = s_F + 9 * NS * WF;          // [10+NS][TX]  staged g_1..g_8, phi(t-1), m_phi(t-1)
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -285,18 +327,50 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
     const int xg = x0 + tid;
     const unsigned pl = P.plane;
     const int nx = P.nx;
+    const int halo_lx = tid < 2 ? tid : TXe + tid;   // halo column of threads 0..3
+    int halo_x = 0;
+    if (tid < 4) {
+        bool xflip;
+        halo_x = map_axis(x0 - 2 + halo_lx, nx, P.wall_x, xflip);
+    }
+
+    // Pipeline of asynchronous copies: the pulled populations of row r+1 are
+    // requested while row r's stages run; the own node's flow populations and
+    // previous-step fields for stage C are requested at the top of the
+    // iteration.  Each thread only reads the staging slots it filled itself.
+    {
+        bool yflip;
+        const int ya = map_axis(y0 - 2, P.ny, P.wall_y, yflip);
+        if (active) prefetch_pull<NS>(P, xg, ya, s_F, WF, tid);
+        if (tid < 4) prefetch_pull<NS>(P, halo_x, ya, s_F, WF, TX + tid);
+        cp_async_commit();
+    }
 
     for (int it = 0; it < TYe + 4; ++it) {
         const int ra = y0 - 2 + it;
+        if (it >= 4 && active) {
+            const int y = ra - 2;
+            unsigned gnode[9];
+            int gdir[9];
+            pull_sources(P, xg, y, gnode, gdir);
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                cp_async4(s_G + (i - 1) * TX + tid, P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+            const unsigned node = (unsigned)y * nx + xg;
+#pragma unroll
+            for (int p = 0; p < NS; ++p) cp_async4(s_G + (8 + p) * TX + tid, P.phi + (size_t)p * pl + node);
+            cp_async4(s_G + (8 + NS) * TX + tid, P.mphi + node);
+            cp_async4(s_G + (9 + NS) * TX + tid, P.mphi + pl + node);
+        }
+        cp_async_commit();
+        cp_async_wait_all_but_one();           // this row's pulled populations have landed
         // ---------------------------------------------------- stage A
         {
-            bool yflip;
-            const int ya = map_axis(ra, P.ny, P.wall_y, yflip);
             const int s5 = slot5(ra);
             if (active) {
                 float ph[NS], plo[NS], jx[NS], jy[NS];
                 const bool own_row = ra >= y0 && ra < y0 + TYe;
-                pull_phi<NS, true>(P, xg, ya, ph, plo, jx, jy);
+                sum_pulled<NS, true>(s_F, WF, tid, ph, plo, jx, jy);
 #pragma unroll
                 for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + tid + 2] = ph[p];
                 if (own_row) {
@@ -310,14 +384,19 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
                 }
             }
             if (tid < 4) {
-                const int lx = tid < 2 ? tid : TXe + tid;
-                bool xflip;
-                const int xx = map_axis(x0 - 2 + lx, nx, P.wall_x, xflip);
                 float ph[NS], plo[NS], jx[NS], jy[NS];
-                pull_phi<NS, false>(P, xx, ya, ph, plo, jx, jy);
+                sum_pulled<NS, false>(s_F, WF, TX + tid, ph, plo, jx, jy);
 #pragma unroll
-                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + lx] = ph[p];
+                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + halo_lx] = ph[p];
             }
+            // request the next row's pulled populations into the same slots
+            if (it + 1 < TYe + 4) {
+                bool yflip;
+                const int yn = map_axis(ra + 1, P.ny, P.wall_y, yflip);
+                if (active) prefetch_pull<NS>(P, xg, yn, s_F, WF, tid);
+                if (tid < 4) prefetch_pull<NS>(P, halo_x, yn, s_F, WF, TX + tid);
+            }
+            cp_async_commit();
         }
         __syncthreads();
         // ---------------------------------------------------- stage B
@@ -367,25 +446,17 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
         if (it >= 4 && active) {
             const int y = ra - 2;
             const unsigned node = (unsigned)y * nx + xg;
-            // previous-step values of this node
+            cp_async_wait_all_but_one();       // this node's g and previous fields have landed
             float php[NS];
 #pragma unroll
-            for (int p = 0; p < NS; ++p) php[p] = P.phi[(size_t)p * pl + node];
-            const float mpx = P.mphi[node], mpy = P.mphi[pl + node];
-            // pulled flow populations g_1..g_8
+            for (int p = 0; p < NS; ++p) php[p] = s_G[(8 + p) * TX + tid];
+            const float mpx = s_G[(8 + NS) * TX + tid], mpy = s_G[(9 + NS) * TX + tid];
             float g[9];
-            {
-                unsigned gnode[9];
-                int gdir[9];
-                pull_sources(P, xg, y, gnode, gdir);
 #pragma unroll
-                for (int i = 1; i < 9; ++i)
-                    g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
-            }
+            for (int i = 1; i < 9; ++i) g[i] = s_G[(i - 1) * TX + tid];
             const int sm = slot5(y - 1), s0 = slot5(y), sp = slot5(y + 1);
             float ph[N], gx[N], gy[N], lap[N];
-            window_grad<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy);
-            window_lap<NS>(s_phi, WP, sm, s0, sp, tid + 2, lap);
+            window_grad_lap<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy, lap);
 
             // mixture density, viscosity and grad rho (Eqs. (11),(12))
             float rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f;
@@ -555,7 +626,8 @@ template <int NS, int MODEL>
 cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
 {
     const size_t smem = sizeof(float) * ((size_t)5 * NS * (tx + 4) + 12 * (size_t)(tx + 2) +
-                                         (size_t)13 * NS * tx);
+                                         (size_t)13 * NS * tx + (size_t)9 * NS * (tx + 4) +
+                                         (size_t)(10 + NS) * tx);
     // The dynamic shared-memory limit is a per-device function attribute.
     static int configured_bytes[64] = {0};
     int dev = 0;
@@ -568,6 +640,26 @@ cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
         if (e != cudaSuccess) return e;
         configured_bytes[dev] = (int)smem;
     }
+    if (ty <= 0) {
+        // Automatic march length: as many row chunks per strip as there are
+        // resident-block slots per strip, so the grid is one full wave.
+        static int cached_slots[64][9] = {{0}};
+        const int tslot = tx / 32;
+        if (tslot < 1 || tslot > 8) return cudaErrorInvalidValue;
+        if (!cached_slots[dev][tslot]) {
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL>, tx, smem);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            cached_slots[dev][tslot] = per_sm * sms > 0 ? per_sm * sms : 1;
+        }
+        const int strips = (p.nx + tx - 1) / tx;
+        const int chunks = cached_slots[dev][tslot] / strips > 0 ? cached_slots[dev][tslot] / strips : 1;
+        ty = (p.ny + chunks - 1) / chunks;
+        if (ty < 16) ty = 16;
+    }
+    if (ty < (p.ny + 65534) / 65535) ty = (p.ny + 65534) / 65535;   // grid.y limit
     dim3 grid((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty);
     step_kernel<NS, MODEL><<<grid, tx, smem, st>>>(p, ty);
     return cudaGetLastError();

@@ -103,10 +103,10 @@ def test_tile_validation(lib):
     # bookkeeping calls are made on it
     h = ctypes.c_void_p(nlbm.nlbm_create(p, 1 << 20, n, 0))
     try:
-        assert nlbm.nlbm_get_tile(h) == (64, 32)
+        assert nlbm.nlbm_get_tile(h) == (64, 0)
         nlbm.nlbm_set_tile(h, 128, 16)
         assert nlbm.nlbm_get_tile(h) == (128, 16)
-        for tx, ty in [(16, 8), (48, 8), (512, 8), (64, 0)]:
+        for tx, ty in [(16, 8), (48, 8), (512, 8), (64, -1)]:
             with pytest.raises(nlbm.NlbmError):
                 nlbm.nlbm_set_tile(h, tx, ty)
         assert nlbm.nlbm_steps_done(h) == 0
