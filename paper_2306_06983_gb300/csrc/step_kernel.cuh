@@ -2,23 +2,28 @@
 // Model A / Model B sources, consistent mass flux, surface tension, F_c,
 // velocity, pressure and both MRT collisions in one pass over the lattice.
 //
-// Work decomposition.  A thread block owns a strip of TX consecutive columns
-// (one thread per column) and marches down TY rows.  The update of row r
-// needs phi(t) on rows r-2..r+2 (F_c differentiates m_phi, which
-// differentiates phi) and m_phi on rows r-1..r+1, so each iteration runs
-// three stages on a rolling window kept in shared memory:
-//   A (row r+2): pull the phase populations, phi_p = sum_i f_i (Eq. (25a)),
-//                for the strip plus two halo columns each side; keep the
-//                first moments j_p of the strip's own nodes;
-//   B (row r+1): grad phi (Eq. (27)), source R_p (Eqs. (2)-(4)) and
-//                m_phi = -M sum_p rho_p (grad phi_p - R_p) (Eq. (13)) for the
-//                strip plus one halo column each side; stage the previous
-//                step's velocity of that row;
-//   C (row r):   Laplacians, chemical potentials and F_s (Eqs. (16)-(17)),
-//                F_c, pull of the flow populations, u and P (Eqs. (25b),
-//                (25c)), both collisions (Eqs. (18)-(24)), stores.
-// Only the halo columns and the 4 + 2 pre-roll rows per strip are computed
-// twice; every population is read from HBM once and written once.
+// Work decomposition.  A thread block of T threads owns a strip of T - 4
+// consecutive columns and marches down TY rows; thread t always works on
+// lattice column x0 - 2 + t.  The update of row r needs phi(t) on rows
+// r-2..r+2 and columns +-2 (F_c differentiates m_phi, which differentiates
+// phi) and m_phi on rows r-1..r+1, columns +-1, so each iteration runs three
+// stages on a rolling window kept in shared memory:
+//   A (row r+2): all T threads sum their pulled phase populations,
+//                phi_p = sum_i f_i (Eq. (25a)); the strip's own nodes keep
+//                j_p and the rounding error of that sum;
+//   B (row r+1): the inner T - 2 threads compute grad phi (Eq. (27)), the
+//                source R_p (Eqs. (2)-(4)) and m_phi = -M sum_p rho_p
+//                (grad phi_p - R_p) (Eq. (13)); the previous step's velocity
+//                of that row is staged;
+//   C (row r):   the inner T - 4 threads (the strip) compute Laplacians,
+//                chemical potentials and F_s (Eqs. (16)-(17)), F_c, u and P
+//                (Eqs. (25b), (25c)), both collisions (Eqs. (18)-(24)), and
+//                store.
+// Every thread runs each stage once per row, so halo columns cost idle
+// lanes, not extra passes.  The pulled populations of the next row are
+// copied into shared memory asynchronously while the current rows are
+// computed.  Only the 4 halo columns and 4 + 2 pre-roll rows per strip are
+// computed twice; every population is read from HBM once and written once.
 //
 // Collision in closed form.  With the relaxation matrix of Sec. 4
 // (S = diag(s0, s1, s1, s2, s2, s2, s3, s3, s4), all entries 1 except
@@ -309,154 +314,118 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
 {
     constexpr int N = NS + 1;
     extern __shared__ float smem[];
-    const int TX = blockDim.x;
-    const int WP = TX + 4, WM = TX + 2;
-    const int WF = TX + 4;                   // staging columns: own nodes, then 4 halo nodes
-    float *s_phi = smem;                     // [5][NS][WP]  phi(t) rows r-2..r+2
-    float *s_m = s_phi + 5 * NS * WP;        // [3][2][WM]   m_phi(t) rows r-1..r+1
-    float *s_u = s_m + 6 * WM;               // [3][2][WM]   u(t-1)   rows r-1..r+1
-    float *s_j = s_u + 6 * WM;               // [3][3NS][TX] j_x, j_y, phi_lo of own nodes
-    float *s_R = s_j + 9 * NS * TX;          // [2][2NS][TX] sources of own nodes
-    float *s_F = s_R + 4 * NS * TX;          // [9NS][WF]    staged pulled f of the next row
-    float *s_G = s_F + 9 * NS * WF;          // [10+NS][TX]  staged g_1..g_8, phi(t-1), m_phi(t-1)
+    // Thread t owns ring column t, lattice column x0 - 2 + t: every thread
+    // pulls one phase field in stage A, the inner T - 2 compute m_phi in
+    // stage B and the inner T - 4 (the strip) complete their node in stage
+    // C, so no warp runs a stage twice for halo nodes.
+    const int T = blockDim.x;
+    const int W = T - 4;                     // strip width
+    float *s_phi = smem;                     // [5][NS][T]   phi(t) rows r-2..r+2
+    float *s_m = s_phi + 5 * NS * T;         // [3][2][T]    m_phi(t) rows r-1..r+1
+    float *s_u = s_m + 6 * T;                // [3][2][T]    u(t-1)   rows r-1..r+1
+    float *s_j = s_u + 6 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
+    float *s_F = s_j + 9 * NS * T;           // [9NS][T]     staged pulled f of the next row
 
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int TXe = min(TX, P.nx - x0), TYe = min(TY, P.ny - y0);
-    const bool active = tid < TXe;
-    const int xg = x0 + tid;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * W, y0 = blockIdx.y * TY;
+    const int We = min(W, P.nx - x0), TYe = min(TY, P.ny - y0);
+    const bool in_ring = t < We + 4;             // phi needed here
+    const bool in_flux = t >= 1 && t < We + 3;   // m_phi needed here
+    const bool own = t >= 2 && t < We + 2;       // node updated here
     const unsigned pl = P.plane;
     const int nx = P.nx;
-    const int halo_lx = tid < 2 ? tid : TXe + tid;   // halo column of threads 0..3
-    int halo_x = 0;
-    if (tid < 4) {
-        bool xflip;
-        halo_x = map_axis(x0 - 2 + halo_lx, nx, P.wall_x, xflip);
-    }
+    bool xflip = false;
+    const int xc = in_ring ? map_axis(x0 - 2 + t, nx, P.wall_x, xflip) : 0;
+    const int xg = x0 - 2 + t;                   // lattice x of an own node
 
-    // Pipeline of asynchronous copies: the pulled populations of row r+1 are
-    // requested while row r's stages run; the own node's flow populations and
-    // previous-step fields for stage C are requested at the top of the
-    // iteration.  Each thread only reads the staging slots it filled itself.
+    // The pulled populations of row r+1 are copied into this thread's
+    // staging slots (cp.async) while rows r..r-2 are computed; each thread
+    // only reads the slots it filled itself.
     {
         bool yflip;
         const int ya = map_axis(y0 - 2, P.ny, P.wall_y, yflip);
-        if (active) prefetch_pull<NS>(P, xg, ya, s_F, WF, tid);
-        if (tid < 4) prefetch_pull<NS>(P, halo_x, ya, s_F, WF, TX + tid);
+        if (in_ring) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
         cp_async_commit();
     }
+    float Rcx[NS], Rcy[NS], Rnx[NS], Rny[NS];   // sources of rows r and r+1 (own node)
+#pragma unroll
+    for (int p = 0; p < NS; ++p) { Rcx[p] = Rcy[p] = Rnx[p] = Rny[p] = 0.f; }
 
     for (int it = 0; it < TYe + 4; ++it) {
         const int ra = y0 - 2 + it;
-        if (it >= 4 && active) {
+        // stage-C inputs of row ra - 2, requested before stages A and B
+        float g[9], php[NS], mpx = 0.f, mpy = 0.f;
+        unsigned node = 0;
+        const bool do_c = it >= 4 && own;
+        if (do_c) {
             const int y = ra - 2;
             unsigned gnode[9];
             int gdir[9];
             pull_sources(P, xg, y, gnode, gdir);
 #pragma unroll
-            for (int i = 1; i < 9; ++i)
-                cp_async4(s_G + (i - 1) * TX + tid, P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
-            const unsigned node = (unsigned)y * nx + xg;
+            for (int i = 1; i < 9; ++i) g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+            node = (unsigned)y * nx + xg;
 #pragma unroll
-            for (int p = 0; p < NS; ++p) cp_async4(s_G + (8 + p) * TX + tid, P.phi + (size_t)p * pl + node);
-            cp_async4(s_G + (8 + NS) * TX + tid, P.mphi + node);
-            cp_async4(s_G + (9 + NS) * TX + tid, P.mphi + pl + node);
+            for (int p = 0; p < NS; ++p) php[p] = P.phi[(size_t)p * pl + node];
+            mpx = P.mphi[node];
+            mpy = P.mphi[pl + node];
         }
-        cp_async_commit();
-        cp_async_wait_all_but_one();           // this row's pulled populations have landed
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this row's pulled f landed
         // ---------------------------------------------------- stage A
-        {
+        if (in_ring) {
+            float ph[NS], plo[NS], jx[NS], jy[NS];
+            sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
             const int s5 = slot5(ra);
-            if (active) {
-                float ph[NS], plo[NS], jx[NS], jy[NS];
-                const bool own_row = ra >= y0 && ra < y0 + TYe;
-                sum_pulled<NS, true>(s_F, WF, tid, ph, plo, jx, jy);
 #pragma unroll
-                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + tid + 2] = ph[p];
-                if (own_row) {
-                    const int s3 = slot3(ra);
+            for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
+            if (own && ra >= y0 && ra < y0 + TYe) {
+                const int s3 = slot3(ra);
 #pragma unroll
-                    for (int p = 0; p < NS; ++p) {
-                        s_j[(s3 * 3 * NS + 3 * p) * TX + tid] = jx[p];
-                        s_j[(s3 * 3 * NS + 3 * p + 1) * TX + tid] = jy[p];
-                        s_j[(s3 * 3 * NS + 3 * p + 2) * TX + tid] = plo[p];
-                    }
+                for (int p = 0; p < NS; ++p) {
+                    s_j[(s3 * 3 * NS + 3 * p) * T + t] = jx[p];
+                    s_j[(s3 * 3 * NS + 3 * p + 1) * T + t] = jy[p];
+                    s_j[(s3 * 3 * NS + 3 * p + 2) * T + t] = plo[p];
                 }
             }
-            if (tid < 4) {
-                float ph[NS], plo[NS], jx[NS], jy[NS];
-                sum_pulled<NS, false>(s_F, WF, TX + tid, ph, plo, jx, jy);
-#pragma unroll
-                for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * WP + halo_lx] = ph[p];
-            }
-            // request the next row's pulled populations into the same slots
             if (it + 1 < TYe + 4) {
                 bool yflip;
                 const int yn = map_axis(ra + 1, P.ny, P.wall_y, yflip);
-                if (active) prefetch_pull<NS>(P, xg, yn, s_F, WF, tid);
-                if (tid < 4) prefetch_pull<NS>(P, halo_x, yn, s_F, WF, TX + tid);
+                prefetch_pull<NS>(P, xc, yn, s_F, T, t);
             }
-            cp_async_commit();
         }
+        cp_async_commit();
         __syncthreads();
         // ---------------------------------------------------- stage B
         if (it >= 2) {
             const int rb = ra - 1;
-            const int sm = slot5(rb - 1), s0 = slot5(rb), sp = slot5(rb + 1);
             const int s3 = slot3(rb);
-            if (active) {
+            if (in_flux) {
                 float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
-                window_grad<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy);
+                window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
                 source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
                 mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
-                s_m[(s3 * 2 + 0) * WM + tid + 1] = mx;
-                s_m[(s3 * 2 + 1) * WM + tid + 1] = my;
-                if (rb >= y0 && rb < y0 + TYe) {
-                    const int s2 = slot2(rb);
+                s_m[(s3 * 2 + 0) * T + t] = mx;
+                s_m[(s3 * 2 + 1) * T + t] = my;
 #pragma unroll
-                    for (int p = 0; p < NS; ++p) {
-                        s_R[(s2 * 2 * NS + 2 * p) * TX + tid] = Rx[p];
-                        s_R[(s2 * 2 * NS + 2 * p + 1) * TX + tid] = Ry[p];
-                    }
-                }
+                for (int p = 0; p < NS; ++p) { Rnx[p] = Rx[p]; Rny[p] = Ry[p]; }
             }
-            if (tid < 2) {
-                const int lm = tid == 0 ? 0 : TXe + 1;
-                float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
-                window_grad<NS>(s_phi, WP, sm, s0, sp, lm + 1, ph, gx, gy);
-                source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
-                mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
-                s_m[(s3 * 2 + 0) * WM + lm] = mx;
-                s_m[(s3 * 2 + 1) * WM + lm] = my;
-            }
-            bool yflip;
-            const int yb = map_axis(rb, P.ny, P.wall_y, yflip);
-            for (int lm = tid; lm < TXe + 2; lm += TX) {
-                bool xflip;
-                const int xb = map_axis(x0 - 1 + lm, nx, P.wall_x, xflip);
-                const unsigned k = (unsigned)yb * nx + xb;
+            if (in_ring) {
+                bool yflip;
+                const int yb = map_axis(rb, P.ny, P.wall_y, yflip);
+                const unsigned k = (unsigned)yb * nx + xc;
                 float ux = __ldg(P.uin + k), uy = __ldg(P.uin + pl + k);
                 if (xflip != yflip) { ux = -ux; uy = -uy; }   // no-slip ghost
-                s_u[(s3 * 2 + 0) * WM + lm] = ux;
-                s_u[(s3 * 2 + 1) * WM + lm] = uy;
+                s_u[(s3 * 2 + 0) * T + t] = ux;
+                s_u[(s3 * 2 + 1) * T + t] = uy;
             }
         }
         __syncthreads();
         // ---------------------------------------------------- stage C
-        if (it >= 4 && active) {
+        if (do_c) {
             const int y = ra - 2;
-            const unsigned node = (unsigned)y * nx + xg;
-            cp_async_wait_all_but_one();       // this node's g and previous fields have landed
-            float php[NS];
-#pragma unroll
-            for (int p = 0; p < NS; ++p) php[p] = s_G[(8 + p) * TX + tid];
-            const float mpx = s_G[(8 + NS) * TX + tid], mpy = s_G[(9 + NS) * TX + tid];
-            float g[9];
-#pragma unroll
-            for (int i = 1; i < 9; ++i) g[i] = s_G[(i - 1) * TX + tid];
             const int sm = slot5(y - 1), s0 = slot5(y), sp = slot5(y + 1);
             float ph[N], gx[N], gy[N], lap[N];
-            window_grad_lap<NS>(s_phi, WP, sm, s0, sp, tid + 2, ph, gx, gy, lap);
+            window_grad_lap<NS>(s_phi, T, sm, s0, sp, t, ph, gx, gy, lap);
 
             // mixture density, viscosity and grad rho (Eqs. (11),(12))
             float rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f;
@@ -498,10 +467,10 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             // with w = m_x u_y - u_x m_y, F_c = (d_y w / 2, -d_x w / 2).
             {
                 const int t3m = slot3(y - 1), t30 = slot3(y), t3p = slot3(y + 1);
-                const int c = tid + 1;
+                const int c = t;
                 auto W = [&](int s, int cc) {
-                    const float mx = s_m[(s * 2) * WM + cc], my = s_m[(s * 2 + 1) * WM + cc];
-                    const float ux = s_u[(s * 2) * WM + cc], uy = s_u[(s * 2 + 1) * WM + cc];
+                    const float mx = s_m[(s * 2) * T + cc], my = s_m[(s * 2 + 1) * T + cc];
+                    const float ux = s_u[(s * 2) * T + cc], uy = s_u[(s * 2 + 1) * T + cc];
                     return mx * uy - ux * my;
                 };
                 const float wsw = W(t3m, c - 1), ws = W(t3m, c), wse = W(t3m, c + 1);
@@ -525,8 +494,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             const float ux = (jgx + 0.5f * Fx) * inv_rho;
             const float uy = (jgy + 0.5f * Fy) * inv_rho;
             const int t30 = slot3(y);
-            const float mphx = s_m[(t30 * 2) * WM + tid + 1], mphy = s_m[(t30 * 2 + 1) * WM + tid + 1];
-            const float upx = s_u[(t30 * 2) * WM + tid + 1], upy = s_u[(t30 * 2 + 1) * WM + tid + 1];
+            const float mphx = s_m[(t30 * 2) * T + t], mphy = s_m[(t30 * 2 + 1) * T + t];
+            const float upx = s_u[(t30 * 2) * T + t], upy = s_u[(t30 * 2 + 1) * T + t];
             const float mx = rho * ux + mphx, my = rho * uy + mphy;
             const float ugr = ux * grx + uy * gry;
             float rho_prev = P.rhoN;
@@ -539,16 +508,15 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             const float Pr = 0.6f * (sg + 0.5f * ugr - (2.f / 3.f) * mu_t + (1.f / 3.f) * (mu_t - mu_prev));
 
             // phase-field collisions, Eqs. (18),(19) in moment space
-            const int s3 = slot3(y), s2 = slot2(y);
+            const int s3 = slot3(y);
             const float s1 = P.s1, c1 = 1.f - s1, h1 = (1.f - 0.5f * s1) * (1.f / 3.f);
 #pragma unroll
             for (int p = 0; p < NS; ++p) {
                 const float phi = ph[p];
-                const float jx = s_j[(s3 * 3 * NS + 3 * p) * TX + tid];
-                const float jy = s_j[(s3 * 3 * NS + 3 * p + 1) * TX + tid];
-                const float plo = s_j[(s3 * 3 * NS + 3 * p + 2) * TX + tid];
-                const float Rx = s_R[(s2 * 2 * NS + 2 * p) * TX + tid];
-                const float Ry = s_R[(s2 * 2 * NS + 2 * p + 1) * TX + tid];
+                const float jx = s_j[(s3 * 3 * NS + 3 * p) * T + t];
+                const float jy = s_j[(s3 * 3 * NS + 3 * p + 1) * T + t];
+                const float plo = s_j[(s3 * 3 * NS + 3 * p + 2) * T + t];
+                const float Rx = Rcx[p], Ry = Rcy[p];
                 // G = d_t(phi u)/c_s^2 + R_p
                 const float Gx = 3.f * (phi * ux - php[p] * upx) + Rx;
                 const float Gy = 3.f * (phi * uy - php[p] * upy) + Ry;
@@ -619,15 +587,15 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             P.mphi[pl + node] = mphy;
             if (P.pout) P.pout[node] = Pr;
         }
+#pragma unroll
+        for (int p = 0; p < NS; ++p) { Rcx[p] = Rnx[p]; Rcy[p] = Rny[p]; }
     }
 }
 
 template <int NS, int MODEL>
 cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * ((size_t)5 * NS * (tx + 4) + 12 * (size_t)(tx + 2) +
-                                         (size_t)13 * NS * tx + (size_t)9 * NS * (tx + 4) +
-                                         (size_t)(10 + NS) * tx);
+    const size_t smem = sizeof(float) * (size_t)tx * (23 * NS + 12);
     // The dynamic shared-memory limit is a per-device function attribute.
     static int configured_bytes[64] = {0};
     int dev = 0;
@@ -654,13 +622,13 @@ cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
             if (e != cudaSuccess) return e;
             cached_slots[dev][tslot] = per_sm * sms > 0 ? per_sm * sms : 1;
         }
-        const int strips = (p.nx + tx - 1) / tx;
+        const int strips = (p.nx + tx - 5) / (tx - 4);
         const int chunks = cached_slots[dev][tslot] / strips > 0 ? cached_slots[dev][tslot] / strips : 1;
         ty = (p.ny + chunks - 1) / chunks;
         if (ty < 16) ty = 16;
     }
     if (ty < (p.ny + 65534) / 65535) ty = (p.ny + 65534) / 65535;   // grid.y limit
-    dim3 grid((p.nx + tx - 1) / tx, (p.ny + ty - 1) / ty);
+    dim3 grid((p.nx + tx - 5) / (tx - 4), (p.ny + ty - 1) / ty);
     step_kernel<NS, MODEL><<<grid, tx, smem, st>>>(p, ty);
     return cudaGetLastError();
 }
