@@ -152,11 +152,11 @@ int64_t nlbm_steps_done(const nlbm_sim *s);
 /* Number of kernels this handle has launched since creation. */
 int64_t nlbm_kernel_launches(const nlbm_sim *s);
 
-/* Tile of the fused step kernel: tx columns per thread block (one thread
- * per column; 32..256, a multiple of 32) marching down ty rows (>= 1), or
- * ty = 0 (the default) to let the library pick the march length that fills
- * the GPU with one wave of blocks.  EINVAL outside those ranges.  Takes
- * effect on the next nlbm_step(). */
+/* Tile of the fused step kernel: tx threads per block (64, 128 or 256; one
+ * thread per column, each block updating a strip of tx - 4 columns) marching
+ * down ty rows (>= 1), or ty = 0 (the default) to let the library pick the
+ * march length that fills the GPU with one wave of blocks.  EINVAL outside
+ * those values.  Takes effect on the next nlbm_step(). */
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
 nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
 

@@ -160,9 +160,8 @@ nlbm_status cuda_fail(nlbm_sim *s, cudaError_t e, const char *what)
 
 void default_tile(nlbm_sim *s)
 {
-    int tx = 128;
-    while (tx > 32 && tx / 2 >= s->kp.nx) tx /= 2;
-    s->tx = tx;
+    // 124-column strips; narrower lattices use 60-column strips
+    s->tx = s->kp.nx > 96 ? 128 : 64;
     s->ty = 0;
 }
 
@@ -421,8 +420,8 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s) { return s ? s->launches : -1; }
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty)
 {
     if (!s) return NLBM_EINVAL;
-    if (tx < 32 || tx > 256 || tx % 32 != 0 || ty < 0) {
-        set_err(s->err, "tile %dx%d outside tx in {32..256, multiple of 32}, ty >= 0", tx, ty);
+    if ((tx != 64 && tx != 128 && tx != 256) || ty < 0) {
+        set_err(s->err, "tile %dx%d outside tx in {64, 128, 256}, ty >= 0", tx, ty);
         return NLBM_EINVAL;
     }
     s->tx = tx;

@@ -309,8 +309,8 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
     my = -P.mob * ay;
 }
 
-template <int NS, int MODEL>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int TY)
+template <int NS, int MODEL, int T>
+__global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int TY)
 {
     constexpr int N = NS + 1;
     extern __shared__ float smem[];
@@ -318,12 +318,10 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
     // pulls one phase field in stage A, the inner T - 2 compute m_phi in
     // stage B and the inner T - 4 (the strip) complete their node in stage
     // C, so no warp runs a stage twice for halo nodes.
-    const int T = blockDim.x;
-    const int W = T - 4;                     // strip width
+    constexpr int W = T - 4;                 // strip width
     float *s_phi = smem;                     // [5][NS][T]   phi(t) rows r-2..r+2
-    float *s_m = s_phi + 5 * NS * T;         // [3][2][T]    m_phi(t) rows r-1..r+1
-    float *s_u = s_m + 6 * T;                // [3][2][T]    u(t-1)   rows r-1..r+1
-    float *s_j = s_u + 6 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
+    float *s_w = s_phi + 5 * NS * T;         // [3][T]       w = m_phi,x u_y - u_x m_phi,y, rows r-1..r+1
+    float *s_j = s_w + 3 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
     float *s_F = s_j + 9 * NS * T;           // [9NS][T]     staged pulled f of the next row
 
     const int t = threadIdx.x;
@@ -347,9 +345,15 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
         if (in_ring) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
         cp_async_commit();
     }
-    float Rcx[NS], Rcy[NS], Rnx[NS], Rny[NS];   // sources of rows r and r+1 (own node)
+    // Values a thread hands from stage B of one row to stage C of the same
+    // row one iteration later (c: row being completed, n: next row), and the
+    // previous-step velocity loaded one iteration ahead of stage B.
+    float Rcx[NS], Rcy[NS], Rnx[NS], Rny[NS];   // sources R_p
 #pragma unroll
     for (int p = 0; p < NS; ++p) { Rcx[p] = Rcy[p] = Rnx[p] = Rny[p] = 0.f; }
+    float Mcx = 0.f, Mcy = 0.f, Mnx = 0.f, Mny = 0.f;   // m_phi(t)
+    float Ucx = 0.f, Ucy = 0.f, Unx = 0.f, Uny = 0.f;   // u(t-1) of the own node
+    float ub_x = 0.f, ub_y = 0.f;                       // u(t-1) for stage B of this iteration
 
     for (int it = 0; it < TYe + 4; ++it) {
         const int ra = y0 - 2 + it;
@@ -369,6 +373,16 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             for (int p = 0; p < NS; ++p) php[p] = P.phi[(size_t)p * pl + node];
             mpx = P.mphi[node];
             mpy = P.mphi[pl + node];
+        }
+        // previous-step velocity of row ra, used by stage B of the next iteration
+        float ua_x = 0.f, ua_y = 0.f;
+        if (in_ring && it >= 1 && it + 1 < TYe + 4) {
+            bool yflip;
+            const int yv = map_axis(ra, P.ny, P.wall_y, yflip);
+            const unsigned k = (unsigned)yv * nx + xc;
+            ua_x = __ldg(P.uin + k);
+            ua_y = __ldg(P.uin + pl + k);
+            if (xflip != yflip) { ua_x = -ua_x; ua_y = -ua_y; }   // no-slip ghost
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this row's pulled f landed
         // ---------------------------------------------------- stage A
@@ -404,19 +418,13 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
                 window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
                 source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
                 mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
-                s_m[(s3 * 2 + 0) * T + t] = mx;
-                s_m[(s3 * 2 + 1) * T + t] = my;
+                s_w[s3 * T + t] = mx * ub_y - ub_x * my;
 #pragma unroll
                 for (int p = 0; p < NS; ++p) { Rnx[p] = Rx[p]; Rny[p] = Ry[p]; }
-            }
-            if (in_ring) {
-                bool yflip;
-                const int yb = map_axis(rb, P.ny, P.wall_y, yflip);
-                const unsigned k = (unsigned)yb * nx + xc;
-                float ux = __ldg(P.uin + k), uy = __ldg(P.uin + pl + k);
-                if (xflip != yflip) { ux = -ux; uy = -uy; }   // no-slip ghost
-                s_u[(s3 * 2 + 0) * T + t] = ux;
-                s_u[(s3 * 2 + 1) * T + t] = uy;
+                Mnx = mx;
+                Mny = my;
+                Unx = ub_x;
+                Uny = ub_y;
             }
         }
         __syncthreads();
@@ -466,16 +474,12 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             // F_c = -div(m_phi u - u m_phi)/2 with the previous velocity:
             // with w = m_x u_y - u_x m_y, F_c = (d_y w / 2, -d_x w / 2).
             {
-                const int t3m = slot3(y - 1), t30 = slot3(y), t3p = slot3(y + 1);
-                const int c = t;
-                auto W = [&](int s, int cc) {
-                    const float mx = s_m[(s * 2) * T + cc], my = s_m[(s * 2 + 1) * T + cc];
-                    const float ux = s_u[(s * 2) * T + cc], uy = s_u[(s * 2 + 1) * T + cc];
-                    return mx * uy - ux * my;
-                };
-                const float wsw = W(t3m, c - 1), ws = W(t3m, c), wse = W(t3m, c + 1);
-                const float ww = W(t30, c - 1), we = W(t30, c + 1);
-                const float wnw = W(t3p, c - 1), wn = W(t3p, c), wne = W(t3p, c + 1);
+                const float *wm = s_w + slot3(y - 1) * T + t;
+                const float *w0 = s_w + slot3(y) * T + t;
+                const float *wp = s_w + slot3(y + 1) * T + t;
+                const float wsw = wm[-1], ws = wm[0], wse = wm[1];
+                const float ww = w0[-1], we = w0[1];
+                const float wnw = wp[-1], wn = wp[0], wne = wp[1];
                 const float dxw = (we - ww) * (1.f / 3.f) + ((wne + wse) - (wnw + wsw)) * (1.f / 12.f);
                 const float dyw = (wn - ws) * (1.f / 3.f) + ((wne + wnw) - (wse + wsw)) * (1.f / 12.f);
                 Fx += 0.5f * dyw;
@@ -493,9 +497,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
             const float inv_rho = 1.f / rho;
             const float ux = (jgx + 0.5f * Fx) * inv_rho;
             const float uy = (jgy + 0.5f * Fy) * inv_rho;
-            const int t30 = slot3(y);
-            const float mphx = s_m[(t30 * 2) * T + t], mphy = s_m[(t30 * 2 + 1) * T + t];
-            const float upx = s_u[(t30 * 2) * T + t], upy = s_u[(t30 * 2 + 1) * T + t];
+            const float mphx = Mcx, mphy = Mcy;
+            const float upx = Ucx, upy = Ucy;
             const float mx = rho * ux + mphx, my = rho * uy + mphy;
             const float ugr = ux * grx + uy * gry;
             float rho_prev = P.rhoN;
@@ -589,13 +592,20 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams P, const int
         }
 #pragma unroll
         for (int p = 0; p < NS; ++p) { Rcx[p] = Rnx[p]; Rcy[p] = Rny[p]; }
+        Mcx = Mnx;
+        Mcy = Mny;
+        Ucx = Unx;
+        Ucy = Uny;
+        ub_x = ua_x;
+        ub_y = ua_y;
     }
 }
 
-template <int NS, int MODEL>
-cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
+template <int NS, int MODEL, int T>
+cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (size_t)tx * (23 * NS + 12);
+    constexpr int tx = T;
+    const size_t smem = sizeof(float) * (size_t)tx * (23 * NS + 3);
     // The dynamic shared-memory limit is a per-device function attribute.
     static int configured_bytes[64] = {0};
     int dev = 0;
@@ -603,7 +613,7 @@ cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if ((int)smem > configured_bytes[dev]) {
-        e = cudaFuncSetAttribute(step_kernel<NS, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         configured_bytes[dev] = (int)smem;
@@ -611,26 +621,35 @@ cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
     if (ty <= 0) {
         // Automatic march length: as many row chunks per strip as there are
         // resident-block slots per strip, so the grid is one full wave.
-        static int cached_slots[64][9] = {{0}};
-        const int tslot = tx / 32;
-        if (tslot < 1 || tslot > 8) return cudaErrorInvalidValue;
-        if (!cached_slots[dev][tslot]) {
+        static int cached_slots[64] = {0};
+        if (!cached_slots[dev]) {
             int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL>, tx, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T>, tx, smem);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
-            cached_slots[dev][tslot] = per_sm * sms > 0 ? per_sm * sms : 1;
+            cached_slots[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
         }
         const int strips = (p.nx + tx - 5) / (tx - 4);
-        const int chunks = cached_slots[dev][tslot] / strips > 0 ? cached_slots[dev][tslot] / strips : 1;
+        const int chunks = cached_slots[dev] / strips > 0 ? cached_slots[dev] / strips : 1;
         ty = (p.ny + chunks - 1) / chunks;
         if (ty < 16) ty = 16;
     }
     if (ty < (p.ny + 65534) / 65535) ty = (p.ny + 65534) / 65535;   // grid.y limit
     dim3 grid((p.nx + tx - 5) / (tx - 4), (p.ny + ty - 1) / ty);
-    step_kernel<NS, MODEL><<<grid, tx, smem, st>>>(p, ty);
+    step_kernel<NS, MODEL, T><<<grid, tx, smem, st>>>(p, ty);
     return cudaGetLastError();
+}
+
+template <int NS, int MODEL>
+cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
+{
+    switch (tx) {
+    case 64: return launch_step_nst<NS, MODEL, 64>(p, ty, st);
+    case 128: return launch_step_nst<NS, MODEL, 128>(p, ty, st);
+    case 256: return launch_step_nst<NS, MODEL, 256>(p, ty, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int MODEL>

@@ -106,7 +106,7 @@ def test_tile_validation(lib):
         assert nlbm.nlbm_get_tile(h) == (64, 0)
         nlbm.nlbm_set_tile(h, 128, 16)
         assert nlbm.nlbm_get_tile(h) == (128, 16)
-        for tx, ty in [(16, 8), (48, 8), (512, 8), (64, -1)]:
+        for tx, ty in [(16, 8), (32, 8), (96, 8), (512, 8), (64, -1)]:
             with pytest.raises(nlbm.NlbmError):
                 nlbm.nlbm_set_tile(h, tx, ty)
         assert nlbm.nlbm_steps_done(h) == 0
