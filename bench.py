@@ -233,26 +233,24 @@ def run_gpu(args):
         stream.synchronize()
 
         # ---------------------------------------------- device-timed region
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one event before every launch and one after the last: launch k
+        # lasts ev[k] -> ev[k+1]; the whole region is ev[0] -> ev[K]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         launches0 = sim.kernel_launches
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clocks:
-            t_start.record(stream)
             for k in range(args.steps):
-                ev[k][0].record(stream)
+                ev[k].record(stream)
                 sim.step(1)
-                ev[k][1].record(stream)
-            t_end.record(stream)
+            ev[args.steps].record(stream)
             torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         launches = sim.kernel_launches - launches0
-        total_ms = t_start.elapsed_time(t_end)
-        per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = ev[0].elapsed_time(ev[args.steps])
+        per_launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         mass = sim.phase_mass(allow_diverged=True)
         tile = list(sim.get_tile())
         sim.close()
