@@ -36,11 +36,15 @@ METRIC = "N-phase LBM MLUPS & % HBM roofline: plain FP32 vs BF16/batched/adjoint
 WORKLOAD = "2048x2048 periodic, N=5, 200 disks (seed 2306), eps=4, M=0.1"
 
 
-def bytes_per_lup(N: int) -> int:
-    """Algorithmic HBM bytes of one lattice update, FP32 storage: each stored
-    value read once and written once -- 9(N-1) phase + 8 flow populations,
-    (N-1) phi + 2 u + 2 m_phi of the previous step."""
-    return 8 * (9 * (N - 1) + 8 + (N - 1) + 4)
+def bytes_per_lup(N: int, storage: str = "f32") -> int:
+    """Algorithmic HBM bytes of one lattice update: each stored value read
+    once and written once.  FP32 storage: 9(N-1) phase + 8 flow populations
+    and (N-1) phi + 2 u + 2 m_phi of the previous step, 4 bytes each.
+    16-bit storage: 8(N-1) phase + 8 flow deviations of 2 bytes, (N-1) FP32
+    rest populations, and (N-1) phi + 2 u + 2 m_phi + 1 P of 4 bytes."""
+    if storage == "f32":
+        return 8 * (9 * (N - 1) + 8 + (N - 1) + 4)
+    return 2 * (2 * (8 * (N - 1) + 8) + 4 * (N - 1) + 4 * ((N - 1) + 5))
 
 
 def kernel_sources_digest() -> str:
@@ -52,10 +56,11 @@ def kernel_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(model: str):
+def measured_traffic(model: str, storage: str = "f32"):
     """DRAM bytes per lattice update of the step kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"step_kernel_model{model}_traffic.txt")
+    suffix = "" if storage == "f32" else f"_{storage}"
+    path = os.path.join(ROOT, "profiles", f"step_kernel_model{model}{suffix}_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -221,6 +226,7 @@ def run_gpu(args):
     else:
         p, phi0 = W.disks_2048(args.model)
         workload = WORKLOAD
+    p = dict(p, storage=args.storage)
     N, nx, ny = p["n_phases"], p["nx"], p["ny"]
     lups = nx * ny
     stream = torch.cuda.Stream()
@@ -289,10 +295,10 @@ def run_gpu(args):
 
     mlups = whole_job_mlups(world, lups, args.steps, total_s)
     avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
-    bpl = bytes_per_lup(N)
+    bpl = bytes_per_lup(N, args.storage)
     achieved = bpl * lups / avg_launch_s / 1e9
     peak, peak_kind = peak_hbm()
-    traffic_bpl = measured_traffic(args.model)
+    traffic_bpl = measured_traffic(args.model, args.storage)
     line = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -300,13 +306,14 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload + f", Model {args.model}", "nx": nx, "ny": ny,
                    "n_phases": N, "model": args.model, "tile": tile,
-                   "l2": f"inputs larger than L2 ({36 * nx * ny * 4 / 1e6:.0f} MB per phase-population "
-                         f"buffer vs 129 MB L2); no flush",
+                   "population_storage": args.storage,
+                   "l2": f"inputs larger than L2 ({bytes_per_lup(N, args.storage) / 2 * nx * ny / 1e6:.0f} MB "
+                         f"of state per step vs 129 MB L2); no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": (round(traffic_bpl * lups) if traffic_bpl else None),
-                     "kernel": f"step_kernel<NS=4, MODEL={args.model}>",
+                     "kernel": f"step_kernel<NS={N - 1}, MODEL={args.model}, storage={args.storage}>",
                      "algorithmic_bytes_per_lup": bpl,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "avg_launch_ms": round(avg_launch_s * 1e3, 5)},
@@ -339,6 +346,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--model", choices=["A", "B"], default="B")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+                    help="population storage: FP32, or 16-bit deviations (FP32 arithmetic)")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--tile", type=int, nargs=2, default=None, metavar=("TX", "TY"))
     ap.add_argument("--lattice", type=int, nargs=2, default=None, metavar=("NX", "NY"),

@@ -54,8 +54,17 @@ typedef enum { NLBM_BC_PERIODIC = 0, NLBM_BC_WALL = 1 } nlbm_bc;
  * exponent n), Model B is Eqs. (3)-(4) (pairwise normals). */
 typedef enum { NLBM_MODEL_A = 0, NLBM_MODEL_B = 1 } nlbm_model;
 
-/* Storage precision of the distribution functions.  Only NLBM_STORE_F32 is
- * implemented; the others return NLBM_ENOTSUP. */
+/* Storage precision of the distribution functions (the arithmetic is FP32
+ * in every form).  NLBM_STORE_F32 keeps every population in FP32.
+ * NLBM_STORE_BF16 / NLBM_STORE_F16 keep the eight moving populations of each
+ * set in 16 bits (bfloat16 / IEEE binary16, round to nearest even) as
+ * deviations from a lattice-weight multiple of a field the reading node
+ * knows: f_i - w_i phi_p(x + c_i) (phi of the node that pulls it, Eq. (19)'s
+ * leading term) and g_i - 3 w_i P(x) (the sending node's pressure, Eq. (22)'s
+ * leading term).  The rest population of each phase set stays FP32 and is
+ * formed so that the values the pullers reconstruct sum to phi_p exactly (up
+ * to one FP32 rounding): per-phase volume (Eq. (1)) is conserved as in FP32.
+ * 16-bit storage needs an even nx (EINVAL otherwise). */
 typedef enum { NLBM_STORE_F32 = 0, NLBM_STORE_BF16 = 1, NLBM_STORE_F16 = 2 } nlbm_storage;
 
 /* The problem statement, in lattice units (dx = dt = 1, c_s^2 = 1/3). */
@@ -92,8 +101,8 @@ nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes);
  * later call is enqueued.  The parameters are copied; the caller may free
  * p->rho, p->mu, p->sigma afterwards.  The state is undefined until
  * nlbm_set_phi().  Errors: EINVAL (bad parameters, NULL pointers, unaligned
- * or too small workspace), ENOTSUP (gravity, reduced storage), ENOMEM (host
- * handle allocation). */
+ * or too small workspace, odd nx with 16-bit storage), ENOTSUP (gravity),
+ * ENOMEM (host handle allocation). */
 nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t workspace_bytes,
                         void *cuda_stream, nlbm_sim **out);
 

@@ -90,7 +90,8 @@ typedef struct {
     int32_t model;      /* 0 = Model A (Eq. 2), 1 = Model B (Eq. 3) */
     int32_t wall_x, wall_y; /* 0 periodic, 1 half-way bounce-back walls */
     int32_t solve_all;  /* 0: N-1 LB sets (paper); 1: all N sets */
-    int32_t pad_;
+    int32_t store16;    /* noise-model build only: 0 none, 1 bfloat16, 2 binary16
+                           rounding of the stored moving populations */
     double model_a_n;   /* exponent n of Model A */
     double eps;         /* interface thickness epsilon */
     double mobility;    /* M */
@@ -385,6 +386,11 @@ static void source_at(const or_params *pp, int N, const real *phi, const real (*
 
 static int valid(const or_params *p)
 {
+#ifdef ORACLE_FP32
+    if (p->store16 < 0 || p->store16 > 2) return 0;
+#else
+    if (p->store16 != 0) return 0;   /* the oracle proper stores exact values */
+#endif
     if (p->nx < 1 || p->ny < 1 || p->n_phases < 2 || p->n_phases > MAXN) return 0;
     if ((p->wall_x && p->nx < 4) || (p->wall_y && p->ny < 4)) return 0;
     if (!(p->eps > 0) || !(p->mobility > 0)) return 0;
@@ -489,6 +495,77 @@ void or_set_phi(void *h, const real *phi_in)
 }
 
 /* ------------------------------------------------------------------ one step */
+
+#ifdef ORACLE_FP32
+/* Noise model of 16-bit population storage (FP32 build only; never a
+ * reference value).  A value v is rounded to nearest-even with p significant
+ * bits: 8 for bfloat16 (FP32 exponent range), 11 for binary16 (normal range
+ * down to 2^-14, fixed quantum 2^-24 below it). */
+static real round16(real v, int mode)
+{
+    if (v == 0 || !isfinite(v)) return v;
+    double a = fabs((double)v);
+    int ex;
+    frexp(a, &ex);                   /* a = m 2^ex, m in [0.5, 1) */
+    int lead = ex - 1;               /* exponent of the leading bit */
+    int p = mode == 1 ? 8 : 11;
+    if (mode == 2 && lead < -14) lead = -14;
+    double q = ldexp(1.0, lead - p + 1);
+    double r = nearbyint(a / q) * q;
+    return (real)copysign(r, (double)v);
+}
+
+/* Streaming with the stored moving populations rounded as deviations from
+ * a lattice-weight multiple of a field the receiving side knows: f_i minus
+ * w_i phi_p of the node that receives it (this step's phi), g_i minus
+ * 3 w_i P of the node that sends it; the rest population keeps each node's
+ * post-collision total.  Same links as the exact streaming. */
+static void stream_store16(or_sim *s)
+{
+    static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const or_params *pp = &s->p;
+    const int nx = pp->nx, ny = pp->ny, L = s->L;
+    const size_t n = s->n;
+    const int mode = pp->store16;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t k = nid(s, x, y);
+            real acc[MAXN], tot[MAXN];
+            for (int p = 0; p < L; p++) {
+                acc[p] = 0;
+                tot[p] = 0;
+                for (int i = 0; i < Q; i++) tot[p] += s->f[(p * Q + i) * n + k];
+            }
+            for (int i = 1; i < Q; i++) {
+                int tx = x + CX[i], ty = y + CY[i];
+                int out_x = tx < 0 || tx >= nx, out_y = ty < 0 || ty >= ny;
+                int bounce = (out_x && pp->wall_x) || (out_y && pp->wall_y);
+                size_t dst;
+                int di;
+                if (bounce) {
+                    dst = k;
+                    di = OPP[i];
+                } else {
+                    tx = (tx % nx + nx) % nx;
+                    ty = (ty % ny + ny) % ny;
+                    dst = nid(s, tx, ty);
+                    di = i;
+                }
+                for (int p = 0; p < L; p++) {
+                    real base = W[i] * s->phi[p * n + dst];
+                    real v = base + round16(s->f[(p * Q + i) * n + k] - base, mode);
+                    s->fn[(p * Q + di) * n + dst] = v;
+                    acc[p] += v;
+                }
+                real gb = 3 * W[i] * s->P[k];
+                s->gn[di * n + dst] = gb + round16(s->g[i * n + k] - gb, mode);
+            }
+            for (int p = 0; p < L; p++) s->fn[(p * Q) * n + k] = tot[p] - acc[p];
+            s->gn[k] = s->g[k];
+        }
+}
+#endif
 
 static void step_once(or_sim *s)
 {
@@ -670,6 +747,10 @@ static void step_once(or_sim *s)
     /* Streaming, Sec. 4: f(x + c_i, t + 1) = f*(x, t); a link that leaves
      * the lattice through a wall is reflected back (half-way bounce-back). */
     static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#ifdef ORACLE_FP32
+    if (pp->store16) stream_store16(s);
+    else
+#endif
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {

@@ -35,7 +35,7 @@ class params_struct(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
         ("n_phases", ctypes.c_int32), ("model", ctypes.c_int32),
         ("wall_x", ctypes.c_int32), ("wall_y", ctypes.c_int32),
-        ("solve_all", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("solve_all", ctypes.c_int32), ("store16", ctypes.c_int32),
         ("model_a_n", ctypes.c_double), ("eps", ctypes.c_double),
         ("mobility", ctypes.c_double),
         ("rho", ctypes.c_double * MAXN), ("mu", ctypes.c_double * MAXN),
@@ -115,8 +115,9 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_params(p: dict, solve_all: bool = False) -> params_struct:
+def make_params(p: dict, solve_all: bool = False, store16: int = 0) -> params_struct:
     s = params_struct()
+    s.store16 = int(store16)
     N = int(p["n_phases"])
     s.nx, s.ny, s.n_phases = int(p["nx"]), int(p["ny"]), N
     s.model = {"A": 0, "B": 1}[p["model"]]
@@ -138,8 +139,12 @@ class OracleSim:
     [N-1, ny, nx]; phase N is 1 - sum."""
 
     def __init__(self, p: dict, phi0: np.ndarray, solve_all: bool = False, threads: int = 0,
-                 fp32: bool = False):
-        """fp32=True runs the FP32 noise-model build instead of the oracle."""
+                 fp32: bool = False, store16: int = 0):
+        """fp32=True runs the FP32 noise-model build instead of the oracle;
+        store16 (1 bfloat16, 2 binary16; noise-model build only) adds the
+        rounding of 16-bit population storage to that noise model."""
+        if store16 and not fp32:
+            raise ValueError("16-bit storage rounding exists only in the FP32 noise model")
         self.fp32 = fp32
         self.lib = oracle_lib_fp32() if fp32 else oracle_lib()
         self._dt = np.float32 if fp32 else np.float64
@@ -147,7 +152,7 @@ class OracleSim:
         self.p = dict(p)
         self.N, self.nx, self.ny = int(p["n_phases"]), int(p["nx"]), int(p["ny"])
         self.threads = threads
-        self._ps = make_params(p, solve_all)
+        self._ps = make_params(p, solve_all, store16)
         self.h = self.lib.or_create(ctypes.byref(self._ps))
         if not self.h:
             raise ValueError("oracle rejected the parameters")

@@ -71,6 +71,50 @@ __global__ void init_kernel(const StepParams P, float *u_other)
     }
 }
 
+// Initial state with 16-bit storage.  The first pull must see the
+// equilibria f_i = w_i phi (Eq. (19)) and g_i = 0: the stored moving
+// deviations are 0 (the puller adds w_i phi of itself, and 3 w_i P with
+// P = 0), and the FP32 rest population of node z is phi(z) minus the eight
+// values z reconstructs, summed with the compensation the step kernel uses.
+__device__ __forceinline__ float init_w(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
+
+template <int NS>
+__global__ void init16_kernel(const StepParams P, float *u_other, float *p_other)
+{
+    const unsigned pl = P.plane;
+    unsigned short *f16 = (unsigned short *)P.fout;
+    unsigned short *g16 = (unsigned short *)P.gout;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            const float phi = P.phi[(size_t)p * pl + k];
+            float r[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) r[i] = __fmaf_rn(init_w(i), phi, 0.f);
+            float e13, e24, e57, e68, ea, eb, es, e0;
+            const float s13 = init_two_sum(r[1], r[3], e13), s24 = init_two_sum(r[2], r[4], e24);
+            const float s57 = init_two_sum(r[5], r[7], e57), s68 = init_two_sum(r[6], r[8], e68);
+            const float sa = init_two_sum(s13, s24, ea), sb = init_two_sum(s57, s68, eb);
+            const float S = init_two_sum(sa, sb, es);
+            const float E = ((e13 + e24) + (e57 + e68)) + ((ea + eb) + es);
+            const float a0 = init_two_sum(phi, -S, e0);
+            P.f0out[(size_t)p * pl + k] = a0 + (e0 - E);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) f16[((size_t)p * 8 + i) * pl + k] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) g16[(size_t)i * pl + k] = 0;
+        P.uout[k] = 0.f;
+        P.uout[pl + k] = 0.f;
+        u_other[k] = 0.f;
+        u_other[pl + k] = 0.f;
+        P.mphi[k] = 0.f;
+        P.mphi[pl + k] = 0.f;
+        P.pout[k] = 0.f;
+        p_other[k] = 0.f;
+    }
+}
+
 template <int NS>
 __global__ void export_kernel(const float *__restrict__ phi_aux, const float *__restrict__ u,
                               const float *__restrict__ Pf, unsigned pl, float *phi_out,
@@ -184,6 +228,17 @@ cudaError_t launch_init(int ns, const StepParams &p, cudaStream_t st)
     // p.uin is the second velocity buffer (both are zeroed).
     const int threads = 256, blocks = grid_for(p.plane, threads);
     float *u_other = const_cast<float *>(p.uin);
+    if (p.f0out) {   // 16-bit storage; p.pin is the second pressure buffer
+        float *p_other = const_cast<float *>(p.pin);
+        switch (ns) {
+#define NLBM_CASE(K) \
+    case K: init16_kernel<K><<<blocks, threads, 0, st>>>(p, u_other, p_other); break;
+            NLBM_CASE(1) NLBM_CASE(2) NLBM_CASE(3) NLBM_CASE(4) NLBM_CASE(5) NLBM_CASE(6) NLBM_CASE(7)
+#undef NLBM_CASE
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (ns) {
 #define NLBM_CASE(K) \
     case K: init_kernel<K><<<blocks, threads, 0, st>>>(p, u_other); break;

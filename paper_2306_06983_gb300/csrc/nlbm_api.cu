@@ -20,11 +20,17 @@ constexpr size_t kMaxPlane = (size_t)1 << 28;   // keeps 9 * plane in 32-bit off
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Workspace layout.  FP32 storage: two copies of f [N-1][9] and g [8]
+// planes, phi and P single (phi is updated in place, P written on request).
+// 16-bit storage: two copies of the f deviations [N-1][8], the FP32 rest
+// populations f0 [N-1], the g deviations [8], phi and P.  f[k] and g[k] are
+// adjacent, so an idle f/g pair can stage N + 3 planes for host downloads.
 struct Layout {
-    size_t f[2], g[2], phi, u[2], mphi, P, partials, mass, total;
+    size_t f[2], g[2], f0[2], phi[2], u[2], mphi, P[2], partials, mass, total;
+    size_t fbytes, gbytes;
 };
 
-Layout make_layout(int ns, size_t plane)
+Layout make_layout(int ns, size_t plane, bool half)
 {
     Layout L{};
     size_t off = 0;
@@ -33,20 +39,28 @@ Layout make_layout(int ns, size_t plane)
         off = align256(off + bytes);
         return o;
     };
-    L.f[0] = take(sizeof(float) * ns * 9 * plane);
-    L.f[1] = take(sizeof(float) * ns * 9 * plane);
-    L.g[0] = take(sizeof(float) * 8 * plane);
-    L.g[1] = take(sizeof(float) * 8 * plane);
-    L.phi = take(sizeof(float) * ns * plane);
+    const size_t es = half ? 2 : 4;
+    L.fbytes = es * ns * (half ? 8 : 9) * plane;
+    L.gbytes = es * 8 * plane;
+    for (int k = 0; k < 2; ++k) {
+        L.f[k] = take(L.fbytes);
+        L.g[k] = take(L.gbytes);
+    }
+    for (int k = 0; k < 2; ++k) L.f0[k] = half ? take(sizeof(float) * ns * plane) : 0;
+    L.phi[0] = take(sizeof(float) * ns * plane);
+    L.phi[1] = half ? take(sizeof(float) * ns * plane) : L.phi[0];
     L.u[0] = take(sizeof(float) * 2 * plane);
     L.u[1] = take(sizeof(float) * 2 * plane);
     L.mphi = take(sizeof(float) * 2 * plane);
-    L.P = take(sizeof(float) * plane);
+    L.P[0] = take(sizeof(float) * plane);
+    L.P[1] = half ? take(sizeof(float) * plane) : L.P[0];
     L.partials = take(sizeof(double) * kMassBlocks * (ns + 2));
     L.mass = take(sizeof(double) * (ns + 2) + sizeof(int));
     L.total = off;
     return L;
 }
+
+bool is_half(int storage) { return storage == NLBM_STORE_BF16 || storage == NLBM_STORE_F16; }
 
 void set_err(char *buf, const char *fmt, ...)
 {
@@ -94,10 +108,10 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
     if (p->reserved != 0) { set_err(err, "reserved must be 0"); return NLBM_EINVAL; }
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) { set_err(err, "gravity not finite"); return NLBM_EINVAL; }
     if (p->gx != 0.0 || p->gy != 0.0) { set_err(err, "gravity is not supported"); return NLBM_ENOTSUP; }
-    if (p->storage == NLBM_STORE_BF16 || p->storage == NLBM_STORE_F16) {
-        set_err(err, "reduced-precision storage is not supported by this build"); return NLBM_ENOTSUP;
+    if (p->storage != NLBM_STORE_F32 && !is_half(p->storage)) { set_err(err, "unknown storage"); return NLBM_EINVAL; }
+    if (is_half(p->storage) && (p->nx & 1)) {
+        set_err(err, "16-bit storage needs an even nx (got %d)", p->nx); return NLBM_EINVAL;
     }
-    if (p->storage != NLBM_STORE_F32) { set_err(err, "unknown storage"); return NLBM_EINVAL; }
     if (kp) {
         memset(kp, 0, sizeof *kp);
         kp->nx = p->nx;
@@ -132,7 +146,7 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
 
 struct nlbm_sim {
     StepParams kp;
-    int N, ns, model;
+    int N, ns, model, storage;
     size_t plane;
     cudaStream_t stream;
     char *ws;
@@ -142,12 +156,14 @@ struct nlbm_sim {
     int64_t launches;
     int tx, ty;
     char err[512];
+    bool half() const { return is_half(storage); }
     float *f(int k) const { return (float *)(ws + L.f[k]); }
     float *g(int k) const { return (float *)(ws + L.g[k]); }
+    float *f0(int k) const { return half() ? (float *)(ws + L.f0[k]) : nullptr; }
     float *u(int k) const { return (float *)(ws + L.u[k]); }
-    float *phi() const { return (float *)(ws + L.phi); }
+    float *phi(int k) const { return (float *)(ws + L.phi[k]); }
     float *mphi() const { return (float *)(ws + L.mphi); }
-    float *P() const { return (float *)(ws + L.P); }
+    float *P(int k) const { return (float *)(ws + L.P[k]); }
 };
 
 namespace {
@@ -168,7 +184,51 @@ void default_tile(nlbm_sim *s)
 // Number of state bytes in a checkpoint, excluding the trailing counter.
 size_t state_payload(const nlbm_sim *s)
 {
-    return sizeof(float) * s->plane * ((size_t)s->ns * 9 + 8 + 2 + s->ns + 2 + 1);
+    const size_t pb = sizeof(float) * s->plane;
+    return s->L.fbytes + s->L.gbytes + (s->half() ? pb * s->ns : 0) + pb * (2 + s->ns + 2 + 1);
+}
+
+// Kernel parameters with the buffers of state a (input) -> b (output).
+StepParams step_params(const nlbm_sim *s, int a, int b)
+{
+    StepParams kp = s->kp;
+    kp.fin = s->f(a);
+    kp.fout = s->f(b);
+    kp.f0in = s->f0(a);
+    kp.f0out = s->f0(b);
+    kp.gin = s->g(a);
+    kp.gout = s->g(b);
+    kp.uin = s->u(a);
+    kp.uout = s->u(b);
+    kp.phi_prev = s->phi(a);
+    kp.phi = s->phi(b);
+    kp.mphi = s->mphi();
+    kp.pin = s->P(a);
+    kp.pout = s->P(b);
+    return kp;
+}
+
+// Initial state into buffers 0 from the phase fields in phi(0).
+cudaError_t launch_initial_state(nlbm_sim *s)
+{
+    // init writes the populations of state 0; kp.uin / kp.pin name the
+    // other velocity / pressure buffers, zeroed as well
+    StepParams kp = step_params(s, 1, 0);
+    kp.phi = s->phi(0);
+    return launch_init(s->ns, kp, s->stream);
+}
+
+cudaError_t launch_step(const nlbm_sim *s, const StepParams &kp)
+{
+    const bool a = s->model == NLBM_MODEL_A;
+    switch (s->storage) {
+    case NLBM_STORE_BF16: return a ? launch_step_a_bf16(s->ns, kp, s->tx, s->ty, s->stream)
+                                   : launch_step_b_bf16(s->ns, kp, s->tx, s->ty, s->stream);
+    case NLBM_STORE_F16: return a ? launch_step_a_f16(s->ns, kp, s->tx, s->ty, s->stream)
+                                  : launch_step_b_f16(s->ns, kp, s->tx, s->ty, s->stream);
+    default: return a ? launch_step_a_f32(s->ns, kp, s->tx, s->ty, s->stream)
+                      : launch_step_b_f32(s->ns, kp, s->tx, s->ty, s->stream);
+    }
 }
 
 }  // namespace
@@ -180,7 +240,7 @@ nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes)
     if (!bytes) { set_err(g_err, "bytes is NULL"); return NLBM_EINVAL; }
     nlbm_status st = validate(p, nullptr, g_err);
     if (st != NLBM_OK) return st;
-    *bytes = make_layout(p->n_phases - 1, (size_t)p->nx * p->ny).total;
+    *bytes = make_layout(p->n_phases - 1, (size_t)p->nx * p->ny, is_half(p->storage)).total;
     return NLBM_OK;
 }
 
@@ -193,7 +253,7 @@ nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t worksp
     nlbm_status st = validate(p, &kp, g_err);
     if (st != NLBM_OK) return st;
     const int ns = p->n_phases - 1;
-    const Layout L = make_layout(ns, (size_t)p->nx * p->ny);
+    const Layout L = make_layout(ns, (size_t)p->nx * p->ny, is_half(p->storage));
     if (!dev_workspace) { set_err(g_err, "workspace is NULL"); return NLBM_EINVAL; }
     if (((uintptr_t)dev_workspace & 255) != 0) { set_err(g_err, "workspace must be 256-byte aligned"); return NLBM_EINVAL; }
     if (workspace_bytes < L.total) {
@@ -206,6 +266,7 @@ nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t worksp
     s->N = p->n_phases;
     s->ns = ns;
     s->model = p->model;
+    s->storage = p->storage;
     s->plane = (size_t)p->nx * p->ny;
     s->stream = (cudaStream_t)cuda_stream;
     s->ws = (char *)dev_workspace;
@@ -222,19 +283,11 @@ nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t worksp
 nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi)
 {
     if (!s || !dev_phi) return NLBM_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(s->phi(), dev_phi, sizeof(float) * s->ns * s->plane,
+    cudaError_t e = cudaMemcpyAsync(s->phi(0), dev_phi, sizeof(float) * s->ns * s->plane,
                                     cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy of the initial phase fields");
-    StepParams kp = s->kp;
     s->cur = 0;
-    kp.fout = s->f(0);
-    kp.gout = s->g(0);
-    kp.uout = s->u(0);
-    kp.uin = s->u(1);
-    kp.phi = s->phi();
-    kp.mphi = s->mphi();
-    kp.pout = s->P();
-    e = launch_init(s->ns, kp, s->stream);
+    e = launch_initial_state(s);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
     s->launches++;
     s->steps = 0;
@@ -244,20 +297,12 @@ nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi)
 nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
 {
     if (!s || !host_phi) return NLBM_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(s->phi(), host_phi, sizeof(float) * s->ns * s->plane,
+    cudaError_t e = cudaMemcpyAsync(s->phi(0), host_phi, sizeof(float) * s->ns * s->plane,
                                     cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "upload of the initial phase fields");
     // the device copy in the phi planes is its own source for the init kernel
-    StepParams kp = s->kp;
     s->cur = 0;
-    kp.fout = s->f(0);
-    kp.gout = s->g(0);
-    kp.uout = s->u(0);
-    kp.uin = s->u(1);
-    kp.phi = s->phi();
-    kp.mphi = s->mphi();
-    kp.pout = s->P();
-    e = launch_init(s->ns, kp, s->stream);
+    e = launch_initial_state(s);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
     s->launches++;
     s->steps = 0;
@@ -267,21 +312,13 @@ nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
 nlbm_status nlbm_step(nlbm_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return NLBM_EINVAL;
-    const int ty = s->ty;   // 0: chosen by the launcher
     for (int64_t k = 0; k < nsteps; ++k) {
-        StepParams kp = s->kp;
         const int a = s->cur, b = s->cur ^ 1;
-        kp.fin = s->f(a);
-        kp.fout = s->f(b);
-        kp.gin = s->g(a);
-        kp.gout = s->g(b);
-        kp.uin = s->u(a);
-        kp.uout = s->u(b);
-        kp.phi = s->phi();
-        kp.mphi = s->mphi();
-        kp.pout = (k == nsteps - 1) ? s->P() : nullptr;
-        cudaError_t e = s->model == NLBM_MODEL_A ? launch_step_model_a(s->ns, kp, s->tx, ty, s->stream)
-                                                 : launch_step_model_b(s->ns, kp, s->tx, ty, s->stream);
+        StepParams kp = step_params(s, a, b);
+        // FP32 storage writes P on the last step of a call only; 16-bit
+        // storage needs it every step (the pullers add 3 w_i P back)
+        if (!s->half() && k != nsteps - 1) kp.pout = nullptr;
+        cudaError_t e = launch_step(s, kp);
         if (e != cudaSuccess) return cuda_fail(s, e, "step kernel");
         s->launches++;
         s->cur = b;
@@ -294,8 +331,8 @@ nlbm_status nlbm_get_moments(nlbm_sim *s, float *dev_phi, float *dev_u, float *d
 {
     if (!s) return NLBM_EINVAL;
     if (!dev_phi && !dev_u && !dev_p) return NLBM_OK;
-    cudaError_t e = launch_export(s->ns, s->phi(), s->u(s->cur), s->P(), (unsigned)s->plane, dev_phi,
-                                  dev_u, dev_p, s->stream);
+    cudaError_t e = launch_export(s->ns, s->phi(s->cur), s->u(s->cur), s->P(s->cur), (unsigned)s->plane,
+                                  dev_phi, dev_u, dev_p, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "export kernel");
     s->launches++;
     return NLBM_OK;
@@ -305,12 +342,12 @@ nlbm_status nlbm_get_moments_host(nlbm_sim *s, float *host_phi, float *host_u, f
 {
     if (!s) return NLBM_EINVAL;
     if (!host_phi && !host_u && !host_p) return NLBM_OK;
-    // Stage through the idle population buffer (it is rewritten by the next
-    // step): N + 3 planes fit in the 9 (N-1) planes of one f copy.
+    // Stage through the idle population buffers (rewritten by the next
+    // step): N + 3 planes fit in one f copy and the g copy after it.
     const size_t pl = s->plane, pb = sizeof(float) * pl;
     float *stage = s->f(s->cur ^ 1);
     float *sphi = stage, *su = stage + (size_t)s->N * pl, *sp = su + 2 * pl;
-    cudaError_t e = launch_export(s->ns, s->phi(), s->u(s->cur), s->P(), (unsigned)pl,
+    cudaError_t e = launch_export(s->ns, s->phi(s->cur), s->u(s->cur), s->P(s->cur), (unsigned)pl,
                                   host_phi ? sphi : nullptr, host_u ? su : nullptr,
                                   host_p ? sp : nullptr, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "export kernel");
@@ -332,7 +369,7 @@ nlbm_status nlbm_phase_mass(nlbm_sim *s, double *host_mass)
     double *partials = (double *)(s->ws + s->L.partials);
     double *mass = (double *)(s->ws + s->L.mass);
     int *flag = (int *)(mass + s->N);
-    cudaError_t e = launch_phase_mass(s->ns, s->phi(), (unsigned)s->plane, partials, mass, flag, s->stream);
+    cudaError_t e = launch_phase_mass(s->ns, s->phi(s->cur), (unsigned)s->plane, partials, mass, flag, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase-mass kernels");
     s->launches += 2;
     double buf[kMaxPhases + 1];
@@ -362,10 +399,12 @@ nlbm_status nlbm_save(nlbm_sim *s, void *dev_dst)
     if (!s || !dev_dst || ((uintptr_t)dev_dst & 15)) return NLBM_EINVAL;
     char *d = (char *)dev_dst;
     const size_t pb = sizeof(float) * s->plane;
+    const int c = s->cur;
     struct Part { const void *src; size_t n; } parts[] = {
-        {s->f(s->cur), pb * s->ns * 9}, {s->g(s->cur), pb * 8}, {s->u(s->cur), pb * 2},
-        {s->phi(), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(), pb}};
+        {s->f(c), s->L.fbytes}, {s->g(c), s->L.gbytes}, {s->f0(c), s->half() ? pb * s->ns : 0},
+        {s->u(c), pb * 2}, {s->phi(c), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(c), pb}};
     for (const Part &pt : parts) {
+        if (!pt.n) continue;
         cudaError_t e = cudaMemcpyAsync(d, pt.src, pt.n, cudaMemcpyDeviceToDevice, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "checkpoint copy");
         d += pt.n;
@@ -385,9 +424,10 @@ nlbm_status nlbm_restore(nlbm_sim *s, const void *dev_src)
     const size_t pb = sizeof(float) * s->plane;
     s->cur = 0;
     struct Part { void *dst; size_t n; } parts[] = {
-        {s->f(0), pb * s->ns * 9}, {s->g(0), pb * 8}, {s->u(0), pb * 2},
-        {s->phi(), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(), pb}};
+        {s->f(0), s->L.fbytes}, {s->g(0), s->L.gbytes}, {s->f0(0), s->half() ? pb * s->ns : 0},
+        {s->u(0), pb * 2}, {s->phi(0), pb * s->ns}, {s->mphi(), pb * 2}, {s->P(0), pb}};
     for (const Part &pt : parts) {
+        if (!pt.n) continue;
         cudaError_t e = cudaMemcpyAsync(pt.dst, d, pt.n, cudaMemcpyDeviceToDevice, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "restore copy");
         d += pt.n;

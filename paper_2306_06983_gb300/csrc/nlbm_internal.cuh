@@ -18,6 +18,10 @@
 //                       step reads it at neighbours for F_c)
 //   mphi [2][plane]     m_phi of the last step
 //   P   [plane]         pressure, written on request
+// With 16-bit storage (bfloat16 or binary16) the moving populations are kept
+// as deviations (f [N-1][8][plane] and g [8][plane], 2 bytes each), the rest
+// populations f0 [N-1][plane] in FP32, and phi and P are double-buffered:
+// the puller adds w_i phi(puller, t) and 3 w_i P(source, t) back.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,21 +46,30 @@ struct StepParams {
     float s1;                  // 1 / tau_f, tau_f = 0.5 + 3 M (Eq. (20))
     float model_n;             // Model A exponent n
     int model_n_int;           // n when it is an integer in 1..8, else 0
-    const float *fin;
+    const float *fin;          // FP32: [N-1][9][plane]; 16-bit: [N-1][8][plane] deviations
     float *fout;
-    const float *gin;
+    const float *f0in;         // 16-bit storage only: FP32 rest populations [N-1][plane]
+    float *f0out;
+    const float *gin;          // FP32: [8][plane]; 16-bit: [8][plane] deviations
     float *gout;
-    float *phi;                // [N-1][plane] in: previous step, out: this step
+    float *phi;                // [N-1][plane] phi of this step (FP32: in place over phi_prev)
+    const float *phi_prev;     // [N-1][plane] phi of the previous step
+    const float *pin;          // 16-bit storage only: P of the previous step
     const float *uin;          // [2][plane] previous step
     float *uout;               // [2][plane] this step
     float *mphi;               // [2][plane] in: previous step, out: this step
     float *pout;               // [plane] or nullptr
 };
 
-// Launchers (defined in step_model_a.cu / step_model_b.cu).  smem bytes and
-// grid are computed by the launcher; returns the launch error.
-cudaError_t launch_step_model_a(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
-cudaError_t launch_step_model_b(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+// Launchers (defined in step_{a,b}_{f32,bf16,f16}.cu: Model A / B, FP32
+// populations or 16-bit deviations).  smem bytes and grid are computed by
+// the launcher; returns the launch error.
+cudaError_t launch_step_a_f32(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_b_f32(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_a_bf16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_b_bf16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_a_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+cudaError_t launch_step_b_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_init(int ns, const StepParams &p, cudaStream_t st);

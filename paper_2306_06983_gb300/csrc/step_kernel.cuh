@@ -35,6 +35,9 @@
 // moment matrix of Eq. (28) is applied in closed form.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "nlbm_internal.cuh"
 
 namespace nlbm {
@@ -169,6 +172,90 @@ __device__ __forceinline__ float inv_norm(float vx, float vy)
 {
     const float n2 = vx * vx + vy * vy;
     return n2 > 1e-24f ? rsqrtf(n2) : 0.0f;
+}
+
+// 16-bit population storage.  The moving populations are stored as
+// deviations from a lattice-weight multiple of a field the puller knows
+// (f_i - w_i phi(puller), g_i - 3 w_i P(source)); the arithmetic stays FP32.
+template <int ST> struct Store16;
+template <> struct Store16<1> {   // bfloat16, round to nearest even
+    static __device__ __forceinline__ unsigned short enc(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ float dec(unsigned h) { return __uint_as_float(h << 16); }
+};
+template <> struct Store16<2> {   // IEEE binary16, round to nearest even
+    static __device__ __forceinline__ unsigned short enc(float v) { return __half_as_ushort(__float2half_rn(v)); }
+    static __device__ __forceinline__ float dec(unsigned h) { return __half2float(__ushort_as_half((unsigned short)h)); }
+};
+
+// Lattice weights w_i (Sec. 4) as FP32 constants; the same constants are
+// used wherever a stored deviation is formed and wherever it is undone.
+__device__ __forceinline__ float w_of(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
+__device__ __forceinline__ int cx_of(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
+__device__ __forceinline__ int cy_of(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
+
+// Staging of the 16-bit populations a ring node pulls.  cp.async moves 4
+// bytes at least, so the aligned word holding each 16-bit value is copied
+// and the half is picked in stage A (par bit i: upper half for direction i;
+// nx is even, so every plane starts on a word boundary and the half is the
+// parity of the source node).  Slots per phase: 0 the FP32 rest population,
+// 1..8 the words of the moving deviations, 9 the puller's own phi(t).
+template <int NS>
+__device__ __forceinline__ unsigned prefetch_pull16(const StepParams &P, int x, int y, float *s_F,
+                                                    int WF, int col)
+{
+    unsigned node[9];
+    int dir[9];
+    pull_sources(P, x, y, node, dir);
+    const unsigned pl = P.plane;
+    const char *f16 = (const char *)P.fin;
+    unsigned par = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) par |= (node[i] & 1u) << i;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        cp_async4(s_F + (p * 10) * WF + col, P.f0in + (size_t)p * pl + node[0]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const size_t e = ((size_t)p * 8 + (unsigned)(dir[i] - 1)) * pl + node[i];
+            cp_async4(s_F + (p * 10 + i) * WF + col, (const float *)(f16 + ((e * 2) & ~(size_t)3)));
+        }
+        cp_async4(s_F + (p * 10 + 9) * WF + col, P.phi_prev + (size_t)p * pl + node[0]);
+    }
+    return par;
+}
+
+// phi and j of one node from its staged 16-bit pull: f_i = w_i phi_own +
+// dev_i (the same FP32 fma the storing node used), summed like sum_pulled.
+template <int NS, int ST, bool OWN>
+__device__ __forceinline__ void sum_pulled16(const float *s_F, int WF, int col, unsigned par,
+                                             float (&ph)[NS], float (&plo)[NS], float (&jx)[NS],
+                                             float (&jy)[NS])
+{
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float own = s_F[(p * 10 + 9) * WF + col];
+        float f[9];
+        f[0] = s_F[(p * 10) * WF + col];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const unsigned wd = __float_as_uint(s_F[(p * 10 + i) * WF + col]);
+            const unsigned h = ((par >> i) & 1u) ? (wd >> 16) : (wd & 0xffffu);
+            f[i] = __fmaf_rn(w_of(i), own, Store16<ST>::dec(h));
+        }
+        float s = f[0], e = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float t = s + f[i];
+            if (OWN) e += f[i] - (t - s);
+            s = t;
+        }
+        ph[p] = s;
+        if (OWN) {
+            plo[p] = e;
+            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        }
+    }
 }
 
 // 3x3 window of the phase fields in the ring: phi, grad phi (Eq. (27)) for
@@ -309,8 +396,8 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
     my = -P.mob * ay;
 }
 
-template <int NS, int MODEL, int T>
-__global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int TY)
+template <int NS, int MODEL, int T, int ST>
+__global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const StepParams P, const int TY)
 {
     constexpr int N = NS + 1;
     extern __shared__ float smem[];
@@ -323,6 +410,7 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
     float *s_w = s_phi + 5 * NS * T;         // [3][T]       w = m_phi,x u_y - u_x m_phi,y, rows r-1..r+1
     float *s_j = s_w + 3 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
     float *s_F = s_j + 9 * NS * T;           // [9NS][T]     staged pulled f of the next row
+                                             // ([10NS][T] with 16-bit storage, see prefetch_pull16)
 
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * W, y0 = blockIdx.y * TY;
@@ -336,13 +424,17 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
     const int xc = in_ring ? map_axis(x0 - 2 + t, nx, P.wall_x, xflip) : 0;
     const int xg = x0 - 2 + t;                   // lattice x of an own node
 
+    unsigned par_next = 0, par_cur = 0;   // halves of the staged 16-bit words
     // The pulled populations of row r+1 are copied into this thread's
     // staging slots (cp.async) while rows r..r-2 are computed; each thread
     // only reads the slots it filled itself.
     {
         bool yflip;
         const int ya = map_axis(y0 - 2, P.ny, P.wall_y, yflip);
-        if (in_ring) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
+        if (in_ring) {
+            if constexpr (ST == 0) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
+            else par_next = prefetch_pull16<NS>(P, xc, ya, s_F, T, t);
+        }
         cp_async_commit();
     }
     // Values a thread hands from stage B of one row to stage C of the same
@@ -367,10 +459,19 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
             int gdir[9];
             pull_sources(P, xg, y, gnode, gdir);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+            for (int i = 1; i < 9; ++i) {
+                if constexpr (ST == 0) {
+                    g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+                } else {
+                    // g_i = 3 w_i P(source) + stored deviation
+                    const unsigned short *g16 = (const unsigned short *)P.gin;
+                    const float dev = Store16<ST>::dec(__ldg(g16 + (unsigned)(gdir[i] - 1) * pl + gnode[i]));
+                    g[i] = __fmaf_rn(3.f * w_of(i), __ldg(P.pin + gnode[i]), dev);
+                }
+            }
             node = (unsigned)y * nx + xg;
 #pragma unroll
-            for (int p = 0; p < NS; ++p) php[p] = P.phi[(size_t)p * pl + node];
+            for (int p = 0; p < NS; ++p) php[p] = P.phi_prev[(size_t)p * pl + node];
             mpx = P.mphi[node];
             mpy = P.mphi[pl + node];
         }
@@ -385,10 +486,12 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
             if (xflip != yflip) { ua_x = -ua_x; ua_y = -ua_y; }   // no-slip ghost
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this row's pulled f landed
+        par_cur = par_next;
         // ---------------------------------------------------- stage A
         if (in_ring) {
             float ph[NS], plo[NS], jx[NS], jy[NS];
-            sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
+            if constexpr (ST == 0) sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
+            else sum_pulled16<NS, ST, true>(s_F, T, t, par_cur, ph, plo, jx, jy);
             const int s5 = slot5(ra);
 #pragma unroll
             for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
@@ -404,7 +507,8 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
             if (it + 1 < TYe + 4) {
                 bool yflip;
                 const int yn = map_axis(ra + 1, P.ny, P.wall_y, yflip);
-                prefetch_pull<NS>(P, xc, yn, s_F, T, t);
+                if constexpr (ST == 0) prefetch_pull<NS>(P, xc, yn, s_F, T, t);
+                else par_next = prefetch_pull16<NS>(P, xc, yn, s_F, T, t);
             }
         }
         cp_async_commit();
@@ -512,6 +616,15 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
 
             // phase-field collisions, Eqs. (18),(19) in moment space
             const int s3 = slot3(y);
+            // links of this node that end in a wall: their population comes
+            // back to this node (half-way bounce-back)
+            const bool bxl = P.wall_x && xg == 0, bxh = P.wall_x && xg == nx - 1;
+            const bool byl = P.wall_y && y == 0, byh = P.wall_y && y == P.ny - 1;
+            auto bounce = [&](int j) {
+                return (cx_of(j) < 0 && bxl) || (cx_of(j) > 0 && bxh) || (cy_of(j) < 0 && byl) ||
+                       (cy_of(j) > 0 && byh);
+            };
+            (void)bounce;
             const float s1 = P.s1, c1 = 1.f - s1, h1 = (1.f - 0.5f * s1) * (1.f / 3.f);
 #pragma unroll
             for (int p = 0; p < NS; ++p) {
@@ -533,26 +646,53 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
                 // (sum_i f_i) - 5 p9 with error-free subtractions, so the
                 // stored populations sum to the pulled ones up to one
                 // rounding (volume conservation, Eq. (1)).
-                const float p9 = phi * (1.f / 9.f), p36 = 0.25f * p9;
-                float f1, f2, f3, f4, f5, f6, f7, f8;
-                exact_pair(p9, 0.5f * (A - D), f1, f3);
-                exact_pair(p9, 0.5f * (B - C), f2, f4);
-                exact_pair(p36, 0.25f * (C + D), f5, f7);
-                exact_pair(p36, 0.25f * (C - D), f6, f8);
-                float e1, e2;
-                const float a1 = two_sum(phi, -4.f * p9, e1);
-                const float a2 = two_sum(a1, -p9, e2);
-                const float f0 = a2 + ((e1 + e2) + plo);
-                float *fo = P.fout + (size_t)p * 9 * pl + node;
-                fo[0 * pl] = f0;
-                fo[1 * pl] = f1;
-                fo[2 * pl] = f2;
-                fo[3 * pl] = f3;
-                fo[4 * pl] = f4;
-                fo[5 * pl] = f5;
-                fo[6 * pl] = f6;
-                fo[7 * pl] = f7;
-                fo[8 * pl] = f8;
+                if constexpr (ST == 0) {
+                    const float p9 = phi * (1.f / 9.f), p36 = 0.25f * p9;
+                    float f1, f2, f3, f4, f5, f6, f7, f8;
+                    exact_pair(p9, 0.5f * (A - D), f1, f3);
+                    exact_pair(p9, 0.5f * (B - C), f2, f4);
+                    exact_pair(p36, 0.25f * (C + D), f5, f7);
+                    exact_pair(p36, 0.25f * (C - D), f6, f8);
+                    float e1, e2;
+                    const float a1 = two_sum(phi, -4.f * p9, e1);
+                    const float a2 = two_sum(a1, -p9, e2);
+                    const float f0 = a2 + ((e1 + e2) + plo);
+                    float *fo = P.fout + (size_t)p * 9 * pl + node;
+                    fo[0 * pl] = f0;
+                    fo[1 * pl] = f1;
+                    fo[2 * pl] = f2;
+                    fo[3 * pl] = f3;
+                    fo[4 * pl] = f4;
+                    fo[5 * pl] = f5;
+                    fo[6 * pl] = f6;
+                    fo[7 * pl] = f7;
+                    fo[8 * pl] = f8;
+                } else {
+                    // f*_j = w_j phi + h_j; stored: dev_j = f*_j - w_j phi(puller of j),
+                    // rounded to 16 bits.  The rest population (FP32) is what
+                    // makes the nine values the pullers reconstruct sum to phi.
+                    const float h1 = 0.5f * (A - D), h2 = 0.5f * (B - C);
+                    const float h5 = 0.25f * (C + D), h6 = 0.25f * (C - D);
+                    const float hdev[9] = {0.f, h1, h2, -h1, -h2, h5, h6, -h5, -h6};
+                    unsigned short *fo16 = (unsigned short *)P.fout + (size_t)p * 8 * pl + node;
+                    float r[9];
+#pragma unroll
+                    for (int j = 1; j < 9; ++j) {
+                        const int sl = cy_of(j) > 0 ? sp : (cy_of(j) < 0 ? sm : s0);
+                        const float base = bounce(j) ? phi : s_phi[(sl * NS + p) * T + t + cx_of(j)];
+                        const unsigned short q = Store16<ST>::enc(__fmaf_rn(w_of(j), phi - base, hdev[j]));
+                        r[j] = __fmaf_rn(w_of(j), base, Store16<ST>::dec(q));
+                        fo16[(size_t)(j - 1) * pl] = q;
+                    }
+                    float e13, e24, e57, e68, ea, eb, es, e0;
+                    const float s13 = two_sum(r[1], r[3], e13), s24 = two_sum(r[2], r[4], e24);
+                    const float s57 = two_sum(r[5], r[7], e57), s68 = two_sum(r[6], r[8], e68);
+                    const float sa = two_sum(s13, s24, ea), sb = two_sum(s57, s68, eb);
+                    const float S = two_sum(sa, sb, es);
+                    const float E = ((e13 + e24) + (e57 + e68)) + ((ea + eb) + es);
+                    const float a0 = two_sum(phi, -S, e0);
+                    P.f0out[(size_t)p * pl + node] = a0 + ((e0 + plo) - E);
+                }
                 P.phi[(size_t)p * pl + node] = phi;
             }
 
@@ -574,15 +714,25 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
                 const float m6 = rho * uy * (1.f / 3.f) + Fy * (1.f / 6.f);
                 const float m7 = rho * ux * (1.f / 3.f) + Fx * (1.f / 6.f);
                 const float m8 = (Pr + Qxx + Qyy) * (1.f / 3.f) + (Mxx + Myy) * (1.f / 6.f) - ugr * (1.f / 18.f);
-                float *go = P.gout + node;
-                go[0 * pl] = 0.5f * ((m1 - m7) + (m3 - m8));
-                go[1 * pl] = 0.5f * ((m2 - m6) + (m4 - m8));
-                go[2 * pl] = 0.5f * ((m7 - m1) + (m3 - m8));
-                go[3 * pl] = 0.5f * ((m6 - m2) + (m4 - m8));
-                go[4 * pl] = 0.25f * ((m5 + m6) + (m7 + m8));
-                go[5 * pl] = 0.25f * ((m6 - m5) + (m8 - m7));
-                go[6 * pl] = 0.25f * ((m5 - m6) + (m8 - m7));
-                go[7 * pl] = 0.25f * ((m7 - m5) + (m8 - m6));
+                const float gs[9] = {0.f,
+                                     0.5f * ((m1 - m7) + (m3 - m8)),
+                                     0.5f * ((m2 - m6) + (m4 - m8)),
+                                     0.5f * ((m7 - m1) + (m3 - m8)),
+                                     0.5f * ((m6 - m2) + (m4 - m8)),
+                                     0.25f * ((m5 + m6) + (m7 + m8)),
+                                     0.25f * ((m6 - m5) + (m8 - m7)),
+                                     0.25f * ((m5 - m6) + (m8 - m7)),
+                                     0.25f * ((m7 - m5) + (m8 - m6))};
+                if constexpr (ST == 0) {
+                    float *go = P.gout + node;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) go[(i - 1) * pl] = gs[i];
+                } else {
+                    // stored: g*_i - 3 w_i P of this node (the puller adds it back)
+                    unsigned short *go = (unsigned short *)P.gout + node;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) go[(size_t)(i - 1) * pl] = Store16<ST>::enc(__fmaf_rn(-3.f * w_of(i), Pr, gs[i]));
+                }
             }
             P.uout[node] = ux;
             P.uout[pl + node] = uy;
@@ -601,11 +751,12 @@ __global__ void __launch_bounds__(T) step_kernel(const StepParams P, const int T
     }
 }
 
-template <int NS, int MODEL, int T>
+template <int NS, int MODEL, int T, int ST>
 cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
     constexpr int tx = T;
-    const size_t smem = sizeof(float) * (size_t)tx * (23 * NS + 3);
+    // phi ring, w ring, own-node j ring, staging (9 slots per phase, 10 with 16-bit storage)
+    const size_t smem = sizeof(float) * (size_t)tx * ((ST == 0 ? 23 : 24) * NS + 3);
     // The dynamic shared-memory limit is a per-device function attribute.
     static int configured_bytes[64] = {0};
     int dev = 0;
@@ -613,7 +764,7 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if ((int)smem > configured_bytes[dev]) {
-        e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         configured_bytes[dev] = (int)smem;
@@ -624,7 +775,7 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
         static int cached_slots[64] = {0};
         if (!cached_slots[dev]) {
             int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T>, tx, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T, ST>, tx, smem);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
@@ -637,32 +788,32 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
     }
     if (ty < (p.ny + 65534) / 65535) ty = (p.ny + 65534) / 65535;   // grid.y limit
     dim3 grid((p.nx + tx - 5) / (tx - 4), (p.ny + ty - 1) / ty);
-    step_kernel<NS, MODEL, T><<<grid, tx, smem, st>>>(p, ty);
+    step_kernel<NS, MODEL, T, ST><<<grid, tx, smem, st>>>(p, ty);
     return cudaGetLastError();
 }
 
-template <int NS, int MODEL>
+template <int NS, int MODEL, int ST>
 cudaError_t launch_step_ns(const StepParams &p, int tx, int ty, cudaStream_t st)
 {
     switch (tx) {
-    case 64: return launch_step_nst<NS, MODEL, 64>(p, ty, st);
-    case 128: return launch_step_nst<NS, MODEL, 128>(p, ty, st);
-    case 256: return launch_step_nst<NS, MODEL, 256>(p, ty, st);
+    case 64: return launch_step_nst<NS, MODEL, 64, ST>(p, ty, st);
+    case 128: return launch_step_nst<NS, MODEL, 128, ST>(p, ty, st);
+    case 256: return launch_step_nst<NS, MODEL, 256, ST>(p, ty, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <int MODEL>
+template <int MODEL, int ST>
 cudaError_t launch_step_model(int ns, const StepParams &p, int tx, int ty, cudaStream_t st)
 {
     switch (ns) {
-    case 1: return launch_step_ns<1, MODEL>(p, tx, ty, st);
-    case 2: return launch_step_ns<2, MODEL>(p, tx, ty, st);
-    case 3: return launch_step_ns<3, MODEL>(p, tx, ty, st);
-    case 4: return launch_step_ns<4, MODEL>(p, tx, ty, st);
-    case 5: return launch_step_ns<5, MODEL>(p, tx, ty, st);
-    case 6: return launch_step_ns<6, MODEL>(p, tx, ty, st);
-    case 7: return launch_step_ns<7, MODEL>(p, tx, ty, st);
+    case 1: return launch_step_ns<1, MODEL, ST>(p, tx, ty, st);
+    case 2: return launch_step_ns<2, MODEL, ST>(p, tx, ty, st);
+    case 3: return launch_step_ns<3, MODEL, ST>(p, tx, ty, st);
+    case 4: return launch_step_ns<4, MODEL, ST>(p, tx, ty, st);
+    case 5: return launch_step_ns<5, MODEL, ST>(p, tx, ty, st);
+    case 6: return launch_step_ns<6, MODEL, ST>(p, tx, ty, st);
+    case 7: return launch_step_ns<7, MODEL, ST>(p, tx, ty, st);
     default: return cudaErrorInvalidValue;
     }
 }

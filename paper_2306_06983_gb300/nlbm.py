@@ -27,6 +27,7 @@ NLBM_OK, NLBM_EINVAL, NLBM_ENOMEM, NLBM_ECUDA, NLBM_ENOTSUP, NLBM_EDIVERGED = ra
 NLBM_BC_PERIODIC, NLBM_BC_WALL = 0, 1
 NLBM_MODEL_A, NLBM_MODEL_B = 0, 1
 NLBM_STORE_F32, NLBM_STORE_BF16, NLBM_STORE_F16 = 0, 1, 2
+STORAGE_CODES = {"f32": NLBM_STORE_F32, "bf16": NLBM_STORE_BF16, "f16": NLBM_STORE_F16}
 STATUS_NAMES = {0: "NLBM_OK", 1: "NLBM_EINVAL", 2: "NLBM_ENOMEM", 3: "NLBM_ECUDA",
                 4: "NLBM_ENOTSUP", 5: "NLBM_EDIVERGED"}
 
@@ -126,7 +127,8 @@ def make_params(p: dict):
     s.sigma = ctypes.cast(sigma, ctypes.POINTER(ctypes.c_double))
     s.gx = float(p.get("gx", 0.0))
     s.gy = float(p.get("gy", 0.0))
-    s.storage = int(p.get("storage", NLBM_STORE_F32))
+    st = p.get("storage", NLBM_STORE_F32)
+    s.storage = STORAGE_CODES[st] if isinstance(st, str) else int(st)
     s.reserved = 0
     return s, (rho, mu, sigma)
 

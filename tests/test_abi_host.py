@@ -44,10 +44,25 @@ def test_workspace_bytes_scales_with_lattice(lib):
     assert abs(b128 / b64 - 4.0) < 0.05
 
 
+def test_workspace_bytes_of_16bit_storage(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    b32 = nlbm.nlbm_workspace_bytes(p)
+    ns, pl = p["n_phases"] - 1, 64 * 64
+    for st in ("bf16", "f16", 1, 2):
+        b16 = nlbm.nlbm_workspace_bytes(dict(p, storage=st))
+        # 2x(8(N-1)+8) 2-byte deviations, 2x(N-1) rest populations, 2x(N-1) phi,
+        # 2x2 u, 2 m_phi, 2 P of 4 bytes
+        need = 2 * (8 * ns + 8) * pl * 2 + (2 * ns + 2 * ns + 4 + 2 + 2) * pl * 4
+        assert need <= b16 < need + 64 * 1024
+        assert b16 < b32
+
+
 @pytest.mark.parametrize("mutate,status", [
     (dict(n_phases=1), 1), (dict(n_phases=9), 1), (dict(nx=0), 1), (dict(eps=0.0), 1),
     (dict(eps=float("nan")), 1), (dict(mobility=-0.1), 1), (dict(model="A", model_a_n=0.0), 1),
-    (dict(gx=1e-5), 4), (dict(storage=1), 4), (dict(storage=7), 1),
+    (dict(gx=1e-5), 4), (dict(storage=1, nx=63), 1), (dict(storage="f16", nx=65), 1),
+    (dict(storage=7), 1),
     (dict(wall_y=True, ny=3), 1),
 ])
 def test_parameter_validation(lib, mutate, status):

@@ -178,3 +178,38 @@ def test_self_sensitivity_envelope(oracle_built):
     assert d.max() > 1e-4            # no FP32 path can meet 1e-5 here
     assert d.mean() < 2e-4
     assert np.abs(a[1] - b[1]).max() < 1e-5
+
+
+def test_store16_noise_model(oracle_built):
+    """The 16-bit-storage noise model (FP32 build only): the FP64 oracle
+    refuses it; at rest on a uniform field every stored deviation is zero, so
+    it equals the plain FP32 build bitwise; on droplets it conserves each
+    phase's volume to FP32 round-off and, over the first steps (before the
+    method's own amplification of rounding takes over), binary16 (11 bits)
+    moves the result less than bfloat16 (8 bits) and more than FP32 alone."""
+    import pytest as _pt
+    p = W.base_params(16, 12, 3, model="B")
+    flat = np.full((2, 12, 16), 0.25)
+    with _pt.raises(ValueError):
+        OracleSim(p, flat, store16=1)
+    a = OracleSim(p, flat, fp32=True)
+    b = OracleSim(p, flat, fp32=True, store16=1)
+    a.step(5)
+    b.step(5)
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
+    p, phi0 = W.droplets_64("B")
+    ref = OracleSim(p, phi0)
+    ref.step(3)
+    d = {}
+    for mode in (1, 2):
+        s = OracleSim(p, phi0, fp32=True, store16=mode)
+        m0 = s.phase_mass()
+        s.step(3)
+        # the noise model sums its volumes in FP32 (4096 terms): 1e-5 relative
+        assert np.all(np.abs(s.phase_mass() - m0) / m0 < 1e-5)
+        d[mode] = np.abs(s.moments()[0] - ref.moments()[0]).max()
+    plain = OracleSim(p, phi0, fp32=True)
+    plain.step(3)
+    d0 = np.abs(plain.moments()[0] - ref.moments()[0]).max()
+    assert d[1] > d[2] > d0
