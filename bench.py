@@ -7,7 +7,14 @@ Workload (one GPU): the 2048x2048 periodic five-phase disk suspension
 advanced one time step = one launch of the fused step kernel.  The
 population buffers (604 MB each) are larger than L2, so no flush is needed.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--model A|B] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--model A|B] [--storage f32|bf16|f16]
+                    [--impl reference] [--no-forms] [--no-cpu-baseline]
+
+Beside the headline the line carries "forms": the same workload with
+bfloat16 / binary16 population storage (throughput, roofline fraction and
+distance to the FP32 fields after the same steps) and the 64-member lens
+ensemble advanced in one persistent launch per step (against one launch per
+member).
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (weak scaling, no collective on the data path); rank 0 prints one
@@ -202,6 +209,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_forms(args, p, phi0, ref_fields, lups, peak):
+    """The other forms of the method, each timed with CUDA events over
+    args.steps steps after args.warmup, beside the headline (FP32) run:
+    16-bit population storage on the same workload (with its distance to the
+    FP32 fields after the same steps), and the 64-member lens ensemble in one
+    persistent launch per step (autotuned tile shape, graph replays) against
+    one launch per member."""
+    import torch
+    from paper_2306_06983_gb300 import workloads as W
+    from paper_2306_06983_gb300.nlbm import Batch, Simulation
+
+    def timed(stream, fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    forms = {}
+    N = p["n_phases"]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for st in ("bf16", "f16"):
+            if st == args.storage:
+                continue
+            sim = Simulation(dict(p, storage=st), stream=stream)
+            sim.set_phi(phi0.astype(np.float32))
+            m0 = sim.phase_mass()
+            sim.step(args.warmup)
+            ms = timed(stream, sim.step, args.steps)
+            phi, u = (t.cpu().numpy() for t in sim.moments()[:2])
+            m1 = sim.phase_mass(allow_diverged=True)
+            sim.close()
+            bpl = bytes_per_lup(N, st)
+            fphi, fu = ref_fields
+            forms[st] = {
+                "value": round(lups / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
+                "algorithmic_bytes_per_lup": bpl,
+                "roofline_frac": round(bpl * lups / (ms / 1e3) / 1e9 / peak, 4),
+                "vs_f32_after_same_steps": {
+                    "steps": args.warmup + args.steps,
+                    "max_abs_dphi": float(np.abs(phi - fphi).max()),
+                    "u_rel_l2": float(np.sqrt(((u - fu) ** 2).sum() / max((fu ** 2).sum(), 1e-300)))},
+                "mass_drift_rel": float((np.abs(m1 - m0) / np.abs(m0)).max()),
+            }
+
+        mem = W.lens_ensemble(64)
+        nodes = sum(q["nx"] * q["ny"] for q, _ in mem)
+        b = Batch([q for q, _ in mem], stream=stream)
+        for k, (_, f0) in enumerate(mem):
+            b.set_phi(k, f0.astype(np.float32))
+        m0 = [b.phase_mass(k) for k in range(len(mem))]
+        b.step(args.warmup)
+        tx, ty, _ = b.autotune(5)
+        l0 = b.kernel_launches
+        ms = timed(stream, b.step, args.steps)
+        launches = b.kernel_launches - l0
+        drift = max(float((np.abs(b.phase_mass(k) - m0[k]) / m0[k]).max()) for k in range(len(mem)))
+        ntiles = b.get_tile()[2]
+        b.close()
+        sims = [Simulation(q, stream=stream) for q, _ in mem]
+        for s_, (_, f0) in zip(sims, mem):
+            s_.set_phi(f0.astype(np.float32))
+            s_.step(args.warmup)
+        n_single = max(10, args.steps // 20)
+        ms1 = timed(stream, lambda n: [s_.step(1) for _ in range(n) for s_ in sims], n_single)
+        for s_ in sims:
+            s_.close()
+        bpl = bytes_per_lup(3)
+        forms["batched"] = {
+            "workload": "64 three-phase lens problems (sizes 128x64, 256x128, 512x256 drawn with seed "
+                        "2306; lens R = 0.2 height on the 1|2 interface; walls top and bottom; sigma_12 = "
+                        "0.01, sigma_13, sigma_23 ~ U[0.005, 0.015]; 32 Model B, 32 Model A with n in "
+                        "0.5..4), FP32",
+            "nodes": nodes, "value": round(nodes / ms / 1e3, 2), "unit": "MLUPS",
+            "ms_per_step": round(ms, 5), "algorithmic_bytes_per_lup": bpl,
+            "roofline_frac": round(bpl * nodes / (ms / 1e3) / 1e9 / peak, 4),
+            "tile": [tx, ty], "tiles_per_step": ntiles, "gpu_launches": launches,
+            "one_launch_per_member_mlups": round(nodes / ms1 / 1e3, 2),
+            "mass_drift_rel_max": drift,
+        }
+    return forms
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -259,6 +352,7 @@ def run_gpu(args):
         per_launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         mass = sim.phase_mass(allow_diverged=True)
         tile = list(sim.get_tile())
+        ref_fields = [t.cpu().numpy() for t in sim.moments()[:2]]
         sim.close()
 
         # ------------------------------------------- end to end, host buffers
@@ -327,6 +421,8 @@ def run_gpu(args):
         "clocks": clocks.summary(),
         "mass_after": [float(v) for v in mass],
     }
+    if not args.no_forms and world == 1:
+        line["forms"] = measure_forms(args, p, phi0, ref_fields, lups, peak)
     if not args.no_cpu_baseline and world == 1:
         from oracle.oracle import build_oracle
         build_oracle()
@@ -354,6 +450,8 @@ def main():
                     help="profiling aid: a disk suspension of this size instead of 2048x2048")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the 16-bit storage and ensemble forms measured beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

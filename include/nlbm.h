@@ -198,6 +198,75 @@ nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
 nlbm_status nlbm_phase_mass_noalloc(const float *dev_phi, int32_t n_phases, int64_t n_nodes,
                                     double *dev_mass, int32_t *dev_flag, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent simulations advanced together.
+ *
+ * Each member is the problem nlbm_create() takes (Secs. 2-4), with its own
+ * lattice size, boundaries, model (A or B, any exponent n), densities,
+ * viscosities, surface tensions, epsilon and mobility -- the kind of sweep
+ * the paper runs case by case (the Model A exponents of Sec. 4, the lens
+ * tension ratios of Sec. 4.3, Table 3).  Members share N and FP32 storage.
+ * One persistent kernel launch per step advances every member: the blocks
+ * resident on the GPU take (member, column strip, row chunk) tiles from a
+ * table ordered largest member first.  Steps of nlbm_batch_step() are
+ * replayed from a captured two-step CUDA graph when the stream is not the
+ * legacy default stream.  Members never exchange data.
+ * ------------------------------------------------------------------------ */
+typedef struct nlbm_batch nlbm_batch;
+
+/* Device workspace bytes for `count` (1..4096) members sims[0..count-1]
+ * (validated as nlbm_workspace_bytes() does; EINVAL if N differs between
+ * members, ENOTSUP for 16-bit storage).  Host only. */
+nlbm_status nlbm_batch_workspace_bytes(const nlbm_params *sims, int32_t count, size_t *bytes);
+
+/* Create an ensemble in caller-owned device memory (256-byte aligned, at
+ * least nlbm_batch_workspace_bytes()); cuda_stream as for nlbm_create().
+ * The member parameters are copied.  Errors as nlbm_create(). */
+nlbm_status nlbm_batch_create(const nlbm_params *sims, int32_t count, void *dev_workspace,
+                              size_t workspace_bytes, void *cuda_stream, nlbm_batch **out);
+
+/* Initial phase fields of member `sim`, as nlbm_set_phi() (dev_phi
+ * [N-1][ny][nx] of that member).  Asynchronous.  Does not reset the other
+ * members or the ensemble's step counter. */
+nlbm_status nlbm_batch_set_phi(nlbm_batch *b, int32_t sim, const float *dev_phi);
+
+/* Advance every member nsteps >= 0 steps: one launch per step, all but the
+ * last from the captured graph.  Asynchronous. */
+nlbm_status nlbm_batch_step(nlbm_batch *b, int64_t nsteps);
+
+/* Moments of member `sim` as nlbm_get_moments() (asynchronous) and its
+ * per-phase volumes as nlbm_phase_mass() (synchronizes). */
+nlbm_status nlbm_batch_get_moments(nlbm_batch *b, int32_t sim, float *dev_phi, float *dev_u, float *dev_p);
+nlbm_status nlbm_batch_phase_mass(nlbm_batch *b, int32_t sim, double *host_mass);
+
+/* Tile shape of the ensemble kernel: tx threads per block (64, 128, 256;
+ * strips of tx - 4 columns) and ty rows per tile (>= 1, 0 = 32).  Rebuilds
+ * the tile table (synchronizes).  get_tile also returns the tile count. */
+nlbm_status nlbm_batch_set_tile(nlbm_batch *b, int32_t tx, int32_t ty);
+nlbm_status nlbm_batch_get_tile(const nlbm_batch *b, int32_t *tx, int32_t *ty, int32_t *ntiles);
+
+/* Bytes of all members' state (the scratch nlbm_batch_autotune() needs). */
+nlbm_status nlbm_batch_state_bytes(const nlbm_batch *b, size_t *bytes);
+
+/* Autotuner: time steps_per_trial (>= 1) ensemble steps (after one untimed
+ * step) for every tile shape tx in {64, 128, 256} x ty in {8, 16, 32, 64,
+ * 128} with CUDA events, restoring the state from dev_scratch (device
+ * memory of at least nlbm_batch_state_bytes()) after each trial, and keep
+ * the fastest.  The state and step counter are unchanged on return; any
+ * output pointer may be NULL.  Synchronizes. */
+nlbm_status nlbm_batch_autotune(nlbm_batch *b, void *dev_scratch, size_t scratch_bytes,
+                                int32_t steps_per_trial, int32_t *best_tx, int32_t *best_ty,
+                                float *best_ms_per_step);
+
+nlbm_status nlbm_batch_synchronize(nlbm_batch *b);
+int64_t nlbm_batch_steps_done(const nlbm_batch *b);
+/* Kernels this ensemble has launched (graph replays count their launches). */
+int64_t nlbm_batch_kernel_launches(const nlbm_batch *b);
+/* Release the ensemble (not the workspace).  Safe on NULL. */
+void nlbm_batch_destroy(nlbm_batch *b);
+/* Text of the ensemble's last error (b may be NULL: last failed create). */
+const char *nlbm_batch_last_error(const nlbm_batch *b);
+
 /* Release the handle (not the workspace).  Safe on NULL.  Does not wait for
  * enqueued work; synchronize first if the workspace is to be reused. */
 void nlbm_destroy(nlbm_sim *s);

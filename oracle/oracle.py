@@ -272,3 +272,77 @@ def flow_force(ugr, Fx, Fy, M2F):
 
 def max_threads() -> int:
     return int(oracle_lib().or_max_threads())
+
+
+# ------------------------------------------------------- closed-form lens pin
+
+def lens_equilibrium(sigma_layer: float, sigma_cap_a: float, sigma_cap_b: float, S: float):
+    """Equilibrium of a lens of area S floating on a flat interface without
+    gravity (Sec. 4.3): Neumann's law fixes the angle each cap makes with the
+    layer interface (law of cosines on the triangle of the three tensions:
+    cos theta_a = (s_layer^2 + s_a^2 - s_b^2) / (2 s_layer s_a)), each cap is
+    a circular arc, and the area fixes the size:
+        d / 2 = sqrt(S / sum_i (theta_i / sin theta_i - cos theta_i) / sin theta_i),
+        h_i = (d / 2) (1 - cos theta_i) / sin theta_i.
+    Cap a is bounded by the interface of tension sigma_cap_a.  Returns
+    (d / 2, h_a, h_b, theta_a, theta_b)."""
+    sl, sa, sb = float(sigma_layer), float(sigma_cap_a), float(sigma_cap_b)
+    ca = (sl * sl + sa * sa - sb * sb) / (2.0 * sl * sa)
+    cb = (sl * sl + sb * sb - sa * sa) / (2.0 * sl * sb)
+    ta, tb = np.arccos(np.clip(ca, -1.0, 1.0)), np.arccos(np.clip(cb, -1.0, 1.0))
+    shape = sum((t / np.sin(t) - np.cos(t)) / np.sin(t) for t in (ta, tb))
+    half_d = np.sqrt(S / shape)
+    ha = half_d * (1.0 - np.cos(ta)) / np.sin(ta)
+    hb = half_d * (1.0 - np.cos(tb)) / np.sin(tb)
+    return half_d, ha, hb, ta, tb
+
+
+def layer_height(phi: np.ndarray, x: int) -> float:
+    """Height of the flat 1|2 interface in column x: where phi_1 - phi_2
+    changes sign (linear interpolation)."""
+    d = phi[0][:, x] - phi[1][:, x]
+    j = int(np.nonzero((d[:-1] > 0) & (d[1:] <= 0))[0][0])
+    return j + d[j] / (d[j] - d[j + 1])
+
+
+def measure_lens(phi: np.ndarray, y_layer: float = None):
+    """Half-length d/2 and the cap heights (below, above) of the lens phase
+    phi[2] = phase 3 from its 0.5 level set, with linear interpolation: the
+    widest chord along the layer height (rows interpolated) and the extent
+    below and above it along the lens's centre column.  The layer height is
+    measured in the column farthest from the lens unless given: the flat
+    interface moves as the lens changes shape, since each layer keeps its
+    volume.  Also returns the lens area sum(phi_3)."""
+    L = phi[2]
+    ny, nx = L.shape
+    if y_layer is None:
+        xc0 = int(np.argmax(L.sum(axis=0)))
+        y_layer = layer_height(phi, (xc0 + nx // 2) % nx)
+    j0 = int(np.floor(y_layer))
+    t = y_layer - j0
+    row = (1.0 - t) * L[j0] + t * L[min(j0 + 1, ny - 1)]
+
+    def extent(v, c):
+        # distance from index c (inside, v >= 0.5) to the 0.5 crossing on each side
+        n = len(v)
+        lo = c
+        while lo - 1 >= 0 and v[lo - 1] >= 0.5:
+            lo -= 1
+        hi = c
+        while hi + 1 < n and v[hi + 1] >= 0.5:
+            hi += 1
+        fl = (lo - 1) + (0.5 - v[lo - 1]) / (v[lo] - v[lo - 1]) if lo > 0 else float(lo)
+        fh = hi + (v[hi] - 0.5) / (v[hi] - v[hi + 1]) if hi + 1 < n else float(hi)
+        return fl, fh
+
+    c = int(np.argmax(row))
+    xl, xh = extent(row, c)
+    xc = 0.5 * (xl + xh)
+    i0 = int(np.floor(xc))
+    s = xc - i0
+    col = (1.0 - s) * L[:, i0] + s * L[:, min(i0 + 1, nx - 1)]
+    jc = int(round(y_layer))
+    if col[jc] < 0.5:
+        jc = int(np.argmax(col))
+    yl, yh = extent(col, jc)
+    return 0.5 * (xh - xl), y_layer - yl, yh - y_layer, float(L.sum())

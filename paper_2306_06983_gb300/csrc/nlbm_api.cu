@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/nlbm.h"
 #include "nlbm_internal.cuh"
@@ -118,6 +120,7 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
         kp->ny = p->ny;
         kp->wall_x = p->bc_x == NLBM_BC_WALL;
         kp->wall_y = p->bc_y == NLBM_BC_WALL;
+        kp->model = p->model;
         kp->plane = (unsigned)((size_t)p->nx * p->ny);
         const double rhoN = p->rho[N - 1], muN = p->mu[N - 1];
         kp->rhoN = (float)rhoN;
@@ -208,13 +211,13 @@ StepParams step_params(const nlbm_sim *s, int a, int b)
     return kp;
 }
 
-// Initial state into buffers 0 from the phase fields in phi(0).
-cudaError_t launch_initial_state(nlbm_sim *s)
+// Initial state into the buffers of state c from the phase fields in phi(c).
+cudaError_t launch_initial_state(nlbm_sim *s, int c)
 {
-    // init writes the populations of state 0; kp.uin / kp.pin name the
+    // init writes the populations of state c; kp.uin / kp.pin name the
     // other velocity / pressure buffers, zeroed as well
-    StepParams kp = step_params(s, 1, 0);
-    kp.phi = s->phi(0);
+    StepParams kp = step_params(s, c ^ 1, c);
+    kp.phi = s->phi(c);
     return launch_init(s->ns, kp, s->stream);
 }
 
@@ -283,11 +286,10 @@ nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t worksp
 nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi)
 {
     if (!s || !dev_phi) return NLBM_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(s->phi(0), dev_phi, sizeof(float) * s->ns * s->plane,
+    cudaError_t e = cudaMemcpyAsync(s->phi(s->cur), dev_phi, sizeof(float) * s->ns * s->plane,
                                     cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy of the initial phase fields");
-    s->cur = 0;
-    e = launch_initial_state(s);
+    e = launch_initial_state(s, s->cur);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
     s->launches++;
     s->steps = 0;
@@ -297,12 +299,11 @@ nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi)
 nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
 {
     if (!s || !host_phi) return NLBM_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(s->phi(0), host_phi, sizeof(float) * s->ns * s->plane,
+    cudaError_t e = cudaMemcpyAsync(s->phi(s->cur), host_phi, sizeof(float) * s->ns * s->plane,
                                     cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "upload of the initial phase fields");
     // the device copy in the phi planes is its own source for the init kernel
-    s->cur = 0;
-    e = launch_initial_state(s);
+    e = launch_initial_state(s, s->cur);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
     s->launches++;
     s->steps = 0;
@@ -478,6 +479,454 @@ nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty)
 }
 
 void nlbm_destroy(nlbm_sim *s) { delete s; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ ensembles
+
+struct nlbm_batch {
+    int count, ns;
+    std::vector<nlbm_sim *> sims;
+    std::vector<size_t> sim_off;         // workspace offset of each simulation
+    size_t state_begin, state_end;       // span of all simulations' state
+    cudaStream_t stream;
+    char *ws;
+    StepParams *d_params;                // [4][count]: parity 0/1 x (no P / P)
+    BatchTile *d_tiles;
+    size_t max_tiles;
+    int ntiles;
+    int *d_counters;                     // [2]
+    int cur;                             // state parity shared by every simulation
+    int tx, ty;
+    cudaGraphExec_t graph;               // two steps (parity 0 then 1), no P output
+    bool graph_ok;
+    int64_t steps, launches;
+    char err[512];
+};
+
+namespace {
+
+constexpr int kBatchMaxSims = 4096;
+
+struct BatchLayout {
+    size_t params, tiles, counters, sims_begin, total;
+    size_t max_tiles;
+    std::vector<size_t> sim_off;
+};
+
+// Largest number of tiles any allowed tile shape gives (tx = 64, ty = 1).
+size_t worst_tiles(const nlbm_params *p, int count)
+{
+    size_t t = 0;
+    for (int k = 0; k < count; ++k) t += (size_t)((p[k].nx + 59) / 60) * (size_t)p[k].ny;
+    return t;
+}
+
+nlbm_status batch_layout(const nlbm_params *p, int count, BatchLayout *B, char *err)
+{
+    if (!p || count < 1 || count > kBatchMaxSims) {
+        set_err(err, "count=%d outside 1..%d (or params NULL)", count, kBatchMaxSims);
+        return NLBM_EINVAL;
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    B->max_tiles = worst_tiles(p, count);
+    B->params = take(sizeof(StepParams) * 4 * (size_t)count);
+    B->tiles = take(sizeof(BatchTile) * B->max_tiles);
+    B->counters = take(2 * sizeof(int));
+    B->sims_begin = off;
+    B->sim_off.resize(count);
+    for (int k = 0; k < count; ++k) {
+        nlbm_status st = validate(&p[k], nullptr, err);
+        if (st != NLBM_OK) {
+            char tmp[512];
+            snprintf(tmp, sizeof tmp, "simulation %d: %s", k, err);
+            memcpy(err, tmp, sizeof tmp);
+            return st;
+        }
+        if (p[k].n_phases != p[0].n_phases) {
+            set_err(err, "simulation %d has N=%d, simulation 0 N=%d: an ensemble shares N", k,
+                    p[k].n_phases, p[0].n_phases);
+            return NLBM_EINVAL;
+        }
+        if (p[k].storage != NLBM_STORE_F32) {
+            set_err(err, "simulation %d: ensembles store FP32 populations", k);
+            return NLBM_ENOTSUP;
+        }
+        B->sim_off[k] = take(make_layout(p[k].n_phases - 1, (size_t)p[k].nx * p[k].ny, false).total);
+    }
+    B->total = off;
+    return NLBM_OK;
+}
+
+nlbm_status batch_fail(nlbm_batch *b, cudaError_t e, const char *what)
+{
+    set_err(b->err, "%s: %s", what, cudaGetErrorString(e));
+    return NLBM_ECUDA;
+}
+
+// Tile table for the current tile shape: every strip and row chunk of every
+// simulation, the largest simulations first (so the last tiles are small).
+nlbm_status build_tiles(nlbm_batch *b)
+{
+    const int W = b->tx - 4;
+    std::vector<int> order(b->count);
+    for (int k = 0; k < b->count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return b->sims[a]->plane > b->sims[c]->plane;
+    });
+    std::vector<BatchTile> t;
+    for (int k : order) {
+        const nlbm_sim *s = b->sims[k];
+        const int nx = s->kp.nx, ny = s->kp.ny;
+        int ty = b->ty > 0 ? b->ty : 32;
+        if (ty > ny) ty = ny;
+        for (int y0 = 0; y0 < ny; y0 += ty)
+            for (int x0 = 0; x0 < nx; x0 += W) t.push_back(BatchTile{k, x0, y0, ty});
+    }
+    if (t.size() > b->max_tiles) {
+        set_err(b->err, "tile table of %zu entries exceeds the %zu reserved", t.size(), b->max_tiles);
+        return NLBM_EINVAL;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_tiles, t.data(), sizeof(BatchTile) * t.size(), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // t is a host temporary
+    if (e != cudaSuccess) return batch_fail(b, e, "upload of the tile table");
+    b->ntiles = (int)t.size();
+    b->graph_ok = false;
+    return NLBM_OK;
+}
+
+nlbm_status upload_params(nlbm_batch *b)
+{
+    std::vector<StepParams> h(4 * (size_t)b->count);
+    for (int par = 0; par < 2; ++par)
+        for (int k = 0; k < b->count; ++k) {
+            StepParams kp = step_params(b->sims[k], par, par ^ 1);
+            kp.pout = nullptr;
+            h[(size_t)(2 * par) * b->count + k] = kp;
+            kp.pout = b->sims[k]->P(0);
+            h[(size_t)(2 * par + 1) * b->count + k] = kp;
+        }
+    cudaError_t e = cudaMemcpyAsync(b->d_params, h.data(), sizeof(StepParams) * h.size(), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "upload of the parameter blocks");
+    return NLBM_OK;
+}
+
+// One step of every simulation from state parity b->cur; with_p selects the
+// parameter blocks that also write P.
+cudaError_t batch_launch(nlbm_batch *b, int parity, bool with_p)
+{
+    const StepParams *tab = b->d_params + (size_t)(2 * parity + (with_p ? 1 : 0)) * b->count;
+    return launch_batch_step(b->ns, b->tx, tab, b->d_tiles, b->ntiles, b->d_counters, parity, b->stream);
+}
+
+void sync_sims(nlbm_batch *b)
+{
+    for (nlbm_sim *s : b->sims) {
+        s->cur = b->cur;
+        s->steps = b->steps;
+    }
+}
+
+nlbm_status capture_graph(nlbm_batch *b)
+{
+    if (b->graph_ok) return NLBM_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, e, "stream capture");
+    cudaError_t e0 = batch_launch(b, 0, false);
+    cudaError_t e1 = batch_launch(b, 1, false);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (e0 != cudaSuccess) e = e0;
+    if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return batch_fail(b, e, "graph of two ensemble steps");
+    b->graph_ok = true;
+    return NLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlbm_status nlbm_batch_workspace_bytes(const nlbm_params *sims, int32_t count, size_t *bytes)
+{
+    if (!bytes) { set_err(g_err, "bytes is NULL"); return NLBM_EINVAL; }
+    BatchLayout B;
+    nlbm_status st = batch_layout(sims, count, &B, g_err);
+    if (st != NLBM_OK) return st;
+    *bytes = B.total;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_create(const nlbm_params *sims, int32_t count, void *dev_workspace, size_t workspace_bytes,
+                              void *cuda_stream, nlbm_batch **out)
+{
+    if (!out) { set_err(g_err, "out is NULL"); return NLBM_EINVAL; }
+    *out = nullptr;
+    BatchLayout B;
+    nlbm_status st = batch_layout(sims, count, &B, g_err);
+    if (st != NLBM_OK) return st;
+    if (!dev_workspace || ((uintptr_t)dev_workspace & 255)) {
+        set_err(g_err, "workspace must be non-NULL and 256-byte aligned");
+        return NLBM_EINVAL;
+    }
+    if (workspace_bytes < B.total) {
+        set_err(g_err, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, B.total);
+        return NLBM_ENOMEM;
+    }
+    nlbm_batch *b = new (std::nothrow) nlbm_batch();
+    if (!b) { set_err(g_err, "host allocation failed"); return NLBM_ENOMEM; }
+    b->count = count;
+    b->ns = sims[0].n_phases - 1;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->ws = (char *)dev_workspace;
+    b->d_params = (StepParams *)(b->ws + B.params);
+    b->d_tiles = (BatchTile *)(b->ws + B.tiles);
+    b->max_tiles = B.max_tiles;
+    b->d_counters = (int *)(b->ws + B.counters);
+    b->sim_off = B.sim_off;
+    b->state_begin = B.sims_begin;
+    b->state_end = B.total;
+    b->cur = 0;
+    b->tx = 128;
+    b->ty = 0;
+    b->graph = nullptr;
+    b->graph_ok = false;
+    b->steps = 0;
+    b->launches = 0;
+    b->err[0] = 0;
+    for (int k = 0; k < count; ++k) {
+        nlbm_sim *s = nullptr;
+        const size_t need = make_layout(b->ns, (size_t)sims[k].nx * sims[k].ny, false).total;
+        st = nlbm_create(&sims[k], b->ws + B.sim_off[k], need, cuda_stream, &s);
+        if (st != NLBM_OK) {
+            for (nlbm_sim *q : b->sims) delete q;
+            delete b;
+            return st;
+        }
+        b->sims.push_back(s);
+    }
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), b->stream);
+    if (e != cudaSuccess) {
+        set_err(g_err, "counter reset: %s", cudaGetErrorString(e));
+        for (nlbm_sim *q : b->sims) delete q;
+        delete b;
+        return NLBM_ECUDA;
+    }
+    if ((st = upload_params(b)) != NLBM_OK || (st = build_tiles(b)) != NLBM_OK) {
+        memcpy(g_err, b->err, sizeof b->err);
+        for (nlbm_sim *q : b->sims) delete q;
+        delete b;
+        return st;
+    }
+    *out = b;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_set_phi(nlbm_batch *b, int32_t sim, const float *dev_phi)
+{
+    if (!b || sim < 0 || sim >= b->count || !dev_phi) return NLBM_EINVAL;
+    nlbm_sim *s = b->sims[sim];
+    s->cur = b->cur;
+    nlbm_status st = nlbm_set_phi(s, dev_phi);
+    b->launches++;
+    if (st != NLBM_OK) memcpy(b->err, s->err, sizeof b->err);
+    return st;
+}
+
+nlbm_status nlbm_batch_step(nlbm_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return NLBM_EINVAL;
+    if (nsteps == 0) return NLBM_OK;
+    int64_t k = 0;
+    const bool use_graph = b->stream != nullptr && nsteps >= 3;
+    cudaError_t e;
+    if (use_graph) {
+        if (b->cur == 1) {   // align to the graph's parity order
+            if ((e = batch_launch(b, 1, false)) != cudaSuccess) return batch_fail(b, e, "ensemble step");
+            b->launches++;
+            b->cur = 0;
+            ++k;
+        }
+        nlbm_status st = capture_graph(b);
+        if (st != NLBM_OK) return st;
+        for (; k + 2 < nsteps; k += 2) {
+            if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return batch_fail(b, e, "graph launch");
+            b->launches += 2;
+        }
+    }
+    for (; k < nsteps; ++k) {
+        if ((e = batch_launch(b, b->cur, k == nsteps - 1)) != cudaSuccess) return batch_fail(b, e, "ensemble step");
+        b->launches++;
+        b->cur ^= 1;
+    }
+    b->steps += nsteps;
+    sync_sims(b);
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_get_moments(nlbm_batch *b, int32_t sim, float *dev_phi, float *dev_u, float *dev_p)
+{
+    if (!b || sim < 0 || sim >= b->count) return NLBM_EINVAL;
+    nlbm_sim *s = b->sims[sim];
+    nlbm_status st = nlbm_get_moments(s, dev_phi, dev_u, dev_p);
+    if (dev_phi || dev_u || dev_p) b->launches++;
+    if (st != NLBM_OK) memcpy(b->err, s->err, sizeof b->err);
+    return st;
+}
+
+nlbm_status nlbm_batch_phase_mass(nlbm_batch *b, int32_t sim, double *host_mass)
+{
+    if (!b || sim < 0 || sim >= b->count || !host_mass) return NLBM_EINVAL;
+    nlbm_sim *s = b->sims[sim];
+    nlbm_status st = nlbm_phase_mass(s, host_mass);
+    b->launches += 2;
+    if (st != NLBM_OK) memcpy(b->err, s->err, sizeof b->err);
+    return st;
+}
+
+nlbm_status nlbm_batch_set_tile(nlbm_batch *b, int32_t tx, int32_t ty)
+{
+    if (!b) return NLBM_EINVAL;
+    if ((tx != 64 && tx != 128 && tx != 256) || ty < 0) {
+        set_err(b->err, "tile %dx%d outside tx in {64, 128, 256}, ty >= 0", tx, ty);
+        return NLBM_EINVAL;
+    }
+    b->tx = tx;
+    b->ty = ty;
+    return build_tiles(b);
+}
+
+nlbm_status nlbm_batch_get_tile(const nlbm_batch *b, int32_t *tx, int32_t *ty, int32_t *ntiles)
+{
+    if (!b || !tx || !ty) return NLBM_EINVAL;
+    *tx = b->tx;
+    *ty = b->ty;
+    if (ntiles) *ntiles = b->ntiles;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_state_bytes(const nlbm_batch *b, size_t *bytes)
+{
+    if (!b || !bytes) return NLBM_EINVAL;
+    *bytes = b->state_end - b->state_begin;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_autotune(nlbm_batch *b, void *dev_scratch, size_t scratch_bytes, int32_t steps_per_trial,
+                                int32_t *best_tx, int32_t *best_ty, float *best_ms_per_step)
+{
+    if (!b || !dev_scratch || steps_per_trial < 1) return NLBM_EINVAL;
+    const size_t span = b->state_end - b->state_begin;
+    if (scratch_bytes < span) {
+        set_err(b->err, "scratch of %zu bytes is smaller than the %zu of state", scratch_bytes, span);
+        return NLBM_ENOMEM;
+    }
+    char *state = b->ws + b->state_begin;
+    const int cur0 = b->cur;
+    cudaError_t e = cudaMemcpyAsync(dev_scratch, state, span, cudaMemcpyDeviceToDevice, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "state copy");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return batch_fail(b, e, "timing events");
+    }
+    static const int kTx[] = {64, 128, 256};
+    static const int kTy[] = {8, 16, 32, 64, 128};
+    float best = 1e30f;
+    int btx = b->tx, bty = b->ty;
+    nlbm_status st = NLBM_OK;
+    for (int tx : kTx) {
+        for (int ty : kTy) {
+            b->tx = tx;
+            b->ty = ty;
+            if ((st = build_tiles(b)) != NLBM_OK) break;
+            // one untimed step, then the timed ones, from the saved state
+            for (int k = 0; k <= steps_per_trial && st == NLBM_OK; ++k) {
+                if (k == 1 && (e = cudaEventRecord(e0, b->stream)) != cudaSuccess) st = batch_fail(b, e, "event");
+                if (st == NLBM_OK && (e = batch_launch(b, b->cur, false)) != cudaSuccess)
+                    st = batch_fail(b, e, "trial step");
+                b->launches++;
+                b->cur ^= 1;
+            }
+            if (st != NLBM_OK) break;
+            float ms = 0.f;
+            if ((e = cudaEventRecord(e1, b->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+                st = batch_fail(b, e, "trial timing");
+                break;
+            }
+            ms /= steps_per_trial;
+            if (ms < best) {
+                best = ms;
+                btx = tx;
+                bty = ty;
+            }
+            // back to the saved state; the tile counters restart from zero
+            // since the parity sequence is broken here
+            b->cur = cur0;
+            if ((e = cudaMemcpyAsync(state, dev_scratch, span, cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(int), b->stream)) != cudaSuccess) {
+                st = batch_fail(b, e, "state restore");
+                break;
+            }
+        }
+        if (st != NLBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cur = cur0;
+    if (st == NLBM_OK) {   // state restored after the last trial
+        b->tx = btx;
+        b->ty = bty;
+        st = build_tiles(b);
+    }
+    if (st == NLBM_OK && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) st = batch_fail(b, e, "synchronize");
+    if (st != NLBM_OK) return st;
+    if (best_tx) *best_tx = btx;
+    if (best_ty) *best_ty = bty;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_batch_synchronize(nlbm_batch *b)
+{
+    if (!b) return NLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "synchronize");
+    return NLBM_OK;
+}
+
+int64_t nlbm_batch_steps_done(const nlbm_batch *b) { return b ? b->steps : -1; }
+
+int64_t nlbm_batch_kernel_launches(const nlbm_batch *b) { return b ? b->launches : -1; }
+
+void nlbm_batch_destroy(nlbm_batch *b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (nlbm_sim *s : b->sims) delete s;
+    delete b;
+}
+
+const char *nlbm_batch_last_error(const nlbm_batch *b) { return b ? b->err : g_err; }
+
+}  // extern "C"
+
+extern "C" {
 
 const char *nlbm_last_error(const nlbm_sim *s) { return s ? s->err : g_err; }
 

@@ -59,6 +59,13 @@ struct StepParams {
     float *uout;               // [2][plane] this step
     float *mphi;               // [2][plane] in: previous step, out: this step
     float *pout;               // [plane] or nullptr
+    int model;                 // 0 Model A, 1 Model B (read by the ensemble kernel)
+};
+
+// One work item of the ensemble kernel: the strip of simulation `sim` that
+// starts at column x0, rows [y0, y0 + ty).
+struct BatchTile {
+    int sim, x0, y0, ty;
 };
 
 // Launchers (defined in step_{a,b}_{f32,bf16,f16}.cu: Model A / B, FP32
@@ -70,6 +77,12 @@ cudaError_t launch_step_a_bf16(int ns, const StepParams &p, int tx, int ty, cuda
 cudaError_t launch_step_b_bf16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 cudaError_t launch_step_a_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 cudaError_t launch_step_b_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+
+// Ensemble of independent simulations (batch.cu): one persistent launch
+// advances every simulation of the table one step; blocks take tiles from
+// d_tiles through the counter d_counters[parity] and clear the other one.
+cudaError_t launch_batch_step(int ns, int tx, const StepParams *d_params, const BatchTile *d_tiles,
+                              int ntiles, int *d_counters, int parity, cudaStream_t st);
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_init(int ns, const StepParams &p, cudaStream_t st);

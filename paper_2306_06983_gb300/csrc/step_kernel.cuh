@@ -396,11 +396,14 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
     my = -P.mob * ay;
 }
 
+// One tile of the fused step: the strip of columns [x0, x0 + T - 4) marching
+// rows [y0, y0 + TY) of the simulation described by P.  smem is the dynamic
+// shared memory of the block (launch_step_nst gives its size).
 template <int NS, int MODEL, int T, int ST>
-__global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const StepParams P, const int TY)
+__device__ __forceinline__ void step_tile(const StepParams &P, const int x0, const int y0, const int TY,
+                                          float *smem)
 {
     constexpr int N = NS + 1;
-    extern __shared__ float smem[];
     // Thread t owns ring column t, lattice column x0 - 2 + t: every thread
     // pulls one phase field in stage A, the inner T - 2 compute m_phi in
     // stage B and the inner T - 4 (the strip) complete their node in stage
@@ -413,7 +416,6 @@ __global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const St
                                              // ([10NS][T] with 16-bit storage, see prefetch_pull16)
 
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * W, y0 = blockIdx.y * TY;
     const int We = min(W, P.nx - x0), TYe = min(TY, P.ny - y0);
     const bool in_ring = t < We + 4;             // phi needed here
     const bool in_flux = t >= 1 && t < We + 3;   // m_phi needed here
@@ -752,11 +754,25 @@ __global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const St
 }
 
 template <int NS, int MODEL, int T, int ST>
+__global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const StepParams P, const int TY)
+{
+    extern __shared__ float smem[];
+    step_tile<NS, MODEL, T, ST>(P, blockIdx.x * (T - 4), blockIdx.y * TY, TY, smem);
+}
+
+// Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
+// the staging rows (9 slots per phase, 10 with 16-bit storage).
+template <int NS, int T, int ST>
+constexpr size_t step_smem_bytes()
+{
+    return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
+}
+
+template <int NS, int MODEL, int T, int ST>
 cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
     constexpr int tx = T;
-    // phi ring, w ring, own-node j ring, staging (9 slots per phase, 10 with 16-bit storage)
-    const size_t smem = sizeof(float) * (size_t)tx * ((ST == 0 ? 23 : 24) * NS + 3);
+    const size_t smem = step_smem_bytes<NS, T, ST>();
     // The dynamic shared-memory limit is a per-device function attribute.
     static int configured_bytes[64] = {0};
     int dev = 0;

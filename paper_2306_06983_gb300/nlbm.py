@@ -79,6 +79,22 @@ def load_library(path: str = LIB_PATH):
         "nlbm_restore": (st, [vp, vp]),
         "nlbm_synchronize": (st, [vp]),
         "nlbm_steps_done": (ctypes.c_int64, [vp]),
+        "nlbm_batch_workspace_bytes": (st, [P(nlbm_params), ctypes.c_int32, P(ctypes.c_size_t)]),
+        "nlbm_batch_create": (st, [P(nlbm_params), ctypes.c_int32, vp, ctypes.c_size_t, vp, P(vp)]),
+        "nlbm_batch_set_phi": (st, [vp, ctypes.c_int32, vp]),
+        "nlbm_batch_step": (st, [vp, ctypes.c_int64]),
+        "nlbm_batch_get_moments": (st, [vp, ctypes.c_int32, vp, vp, vp]),
+        "nlbm_batch_phase_mass": (st, [vp, ctypes.c_int32, P(ctypes.c_double)]),
+        "nlbm_batch_set_tile": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "nlbm_batch_get_tile": (st, [vp, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "nlbm_batch_state_bytes": (st, [vp, P(ctypes.c_size_t)]),
+        "nlbm_batch_autotune": (st, [vp, vp, ctypes.c_size_t, ctypes.c_int32, P(ctypes.c_int32),
+                                     P(ctypes.c_int32), P(ctypes.c_float)]),
+        "nlbm_batch_synchronize": (st, [vp]),
+        "nlbm_batch_steps_done": (ctypes.c_int64, [vp]),
+        "nlbm_batch_kernel_launches": (ctypes.c_int64, [vp]),
+        "nlbm_batch_destroy": (None, [vp]),
+        "nlbm_batch_last_error": (ctypes.c_char_p, [vp]),
         "nlbm_kernel_launches": (ctypes.c_int64, [vp]),
         "nlbm_set_tile": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
         "nlbm_get_tile": (st, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
@@ -337,3 +353,178 @@ class Simulation:
 
     def get_tile(self):
         return nlbm_get_tile(self.h)
+
+
+# ------------------------------------------------------------ ensembles
+
+def _check_batch(st: int, handle=None):
+    if st != NLBM_OK:
+        msg = load_library().nlbm_batch_last_error(handle).decode()
+        raise NlbmError(st, msg)
+
+
+def _params_array(sims):
+    arr = (nlbm_params * len(sims))()
+    keep = []
+    for k, p in enumerate(sims):
+        s, kp = make_params(p)
+        arr[k] = s
+        keep.append(kp)
+    return arr, keep
+
+
+def nlbm_batch_workspace_bytes(sims) -> int:
+    arr, keep = _params_array(sims)
+    out = ctypes.c_size_t(0)
+    _check_batch(load_library().nlbm_batch_workspace_bytes(arr, len(sims), ctypes.byref(out)))
+    return int(out.value)
+
+
+def nlbm_batch_create(sims, workspace_ptr: int, workspace_bytes: int, stream_ptr: int) -> int:
+    arr, keep = _params_array(sims)
+    h = ctypes.c_void_p()
+    _check_batch(load_library().nlbm_batch_create(arr, len(sims), ctypes.c_void_p(workspace_ptr),
+                                                  workspace_bytes, ctypes.c_void_p(stream_ptr),
+                                                  ctypes.byref(h)))
+    return h.value
+
+
+def nlbm_batch_set_phi(h, sim: int, dev_ptr: int):
+    _check_batch(load_library().nlbm_batch_set_phi(h, sim, ctypes.c_void_p(dev_ptr)), h)
+
+
+def nlbm_batch_step(h, nsteps: int):
+    _check_batch(load_library().nlbm_batch_step(h, nsteps), h)
+
+
+def nlbm_batch_get_moments(h, sim: int, phi_ptr=None, u_ptr=None, p_ptr=None):
+    _check_batch(load_library().nlbm_batch_get_moments(h, sim, phi_ptr, u_ptr, p_ptr), h)
+
+
+def nlbm_batch_phase_mass(h, sim: int, N: int) -> np.ndarray:
+    out = (ctypes.c_double * N)()
+    _check_batch(load_library().nlbm_batch_phase_mass(h, sim, out), h)
+    return np.array(out[:], dtype=np.float64)
+
+
+def nlbm_batch_set_tile(h, tx: int, ty: int):
+    _check_batch(load_library().nlbm_batch_set_tile(h, tx, ty), h)
+
+
+def nlbm_batch_get_tile(h):
+    tx, ty, nt = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check_batch(load_library().nlbm_batch_get_tile(h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(nt)), h)
+    return tx.value, ty.value, nt.value
+
+
+def nlbm_batch_state_bytes(h) -> int:
+    out = ctypes.c_size_t(0)
+    _check_batch(load_library().nlbm_batch_state_bytes(h, ctypes.byref(out)), h)
+    return int(out.value)
+
+
+def nlbm_batch_autotune(h, scratch_ptr: int, scratch_bytes: int, steps_per_trial: int):
+    tx, ty, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check_batch(load_library().nlbm_batch_autotune(h, ctypes.c_void_p(scratch_ptr), scratch_bytes,
+                                                    steps_per_trial, ctypes.byref(tx), ctypes.byref(ty),
+                                                    ctypes.byref(ms)), h)
+    return tx.value, ty.value, ms.value
+
+
+def nlbm_batch_synchronize(h):
+    _check_batch(load_library().nlbm_batch_synchronize(h), h)
+
+
+def nlbm_batch_steps_done(h) -> int:
+    return int(load_library().nlbm_batch_steps_done(h))
+
+
+def nlbm_batch_kernel_launches(h) -> int:
+    return int(load_library().nlbm_batch_kernel_launches(h))
+
+
+def nlbm_batch_destroy(h):
+    load_library().nlbm_batch_destroy(h)
+
+
+def nlbm_batch_last_error(h=None) -> str:
+    return load_library().nlbm_batch_last_error(h).decode()
+
+
+class Batch:
+    """An ensemble of independent simulations on the current CUDA device; the
+    workspace is a torch uint8 tensor owned by this object."""
+
+    def __init__(self, sims, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.sims = [dict(p) for p in sims]
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = nlbm_batch_workspace_bytes(self.sims)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.h = ctypes.c_void_p(nlbm_batch_create(self.sims, aligned, nbytes, self.stream.cuda_stream))
+        self._phi0 = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            nlbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.sims)
+
+    def set_phi(self, k: int, phi0):
+        p = self.sims[k]
+        N, ny, nx = int(p["n_phases"]), int(p["ny"]), int(p["nx"])
+        t = self.torch.as_tensor(phi0).to(device=self.device, dtype=self.torch.float32).contiguous()
+        if t.shape != (N - 1, ny, nx):
+            raise ValueError(f"phi0 of member {k} has shape {tuple(t.shape)}, expected {(N - 1, ny, nx)}")
+        self._phi0[k] = t
+        nlbm_batch_set_phi(self.h, k, t.data_ptr())
+
+    def step(self, n: int):
+        nlbm_batch_step(self.h, n)
+
+    def moments(self, k: int):
+        torch = self.torch
+        p = self.sims[k]
+        N, ny, nx = int(p["n_phases"]), int(p["ny"]), int(p["nx"])
+        phi = torch.empty((N, ny, nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((2, ny, nx), dtype=torch.float32, device=self.device)
+        P = torch.empty((ny, nx), dtype=torch.float32, device=self.device)
+        nlbm_batch_get_moments(self.h, k, phi.data_ptr(), u.data_ptr(), P.data_ptr())
+        return phi, u, P
+
+    def phase_mass(self, k: int) -> np.ndarray:
+        return nlbm_batch_phase_mass(self.h, k, int(self.sims[k]["n_phases"]))
+
+    def set_tile(self, tx: int, ty: int):
+        nlbm_batch_set_tile(self.h, tx, ty)
+
+    def get_tile(self):
+        return nlbm_batch_get_tile(self.h)
+
+    def autotune(self, steps_per_trial: int = 5):
+        n = nlbm_batch_state_bytes(self.h)
+        scratch = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        return nlbm_batch_autotune(self.h, scratch.data_ptr(), n, steps_per_trial)
+
+    def synchronize(self):
+        nlbm_batch_synchronize(self.h)
+
+    @property
+    def steps_done(self) -> int:
+        return nlbm_batch_steps_done(self.h)
+
+    @property
+    def kernel_launches(self) -> int:
+        return nlbm_batch_kernel_launches(self.h)

@@ -197,3 +197,48 @@ def random_smooth(nx, ny, N, seed=SEED, model="B", model_a_n=1.0, eps=4.0,
     p = base_params(nx, ny, N, model=model, model_a_n=model_a_n, eps=eps, mobility=0.1,
                     rho=rho, mu=rho * nu, sigma=sig, wall_x=wall_x, wall_y=wall_y)
     return p, phi[:N - 1].copy()
+
+
+def lens(nx, ny, R, s12, s13, s23, model="B", model_a_n=1.0, eps=4.0, mobility=0.1,
+         y0=None, cx=None):
+    """Ternary liquid lens (Sec. 4.3's problem, relabelled): phase 1 the lower
+    layer, phase 2 the upper layer, phase 3 (the unsolved phase) a disk of
+    radius R centred on their flat interface at height y0 (default ny/2 - 0.5,
+    midway between the walls).  Periodic in x, no-flux walls at the bottom and
+    top.  Profiles as in Sec. 4.3: the disk 0.5 + 0.5 tanh((R - r)/(eps/2)),
+    the layers 0.5 + 0.5 tanh(2 (y0 - y)/eps) outside it.  Densities 1,
+    relaxation time 1 (mu = rho/6), mobility 0.1 unless given."""
+    y0 = ny / 2.0 - 0.5 if y0 is None else float(y0)
+    cx = nx / 2.0 - 0.5 if cx is None else float(cx)
+    L = disk(nx, ny, cx, y0, R, eps, periodic_x=True, periodic_y=False)
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    B = 0.5 + 0.5 * np.tanh(2.0 * (y0 - y) / eps)
+    sig = [[0.0, s12, s13], [s12, 0.0, s23], [s13, s23, 0.0]]
+    p = base_params(nx, ny, 3, model=model, model_a_n=model_a_n, eps=eps, mobility=mobility,
+                    sigma=sig, wall_y=True)
+    phi0 = np.stack([(1.0 - L) * B, (1.0 - L) * (1.0 - B)])
+    return p, phi0
+
+
+LENS_SIZES = ((128, 64), (256, 128), (512, 256))
+MODEL_A_SWEEP = (0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0)
+
+
+def lens_ensemble(count=64, seed=SEED, sizes=LENS_SIZES):
+    """Ensemble of independent three-phase lens problems: lattice sizes drawn
+    from `sizes`, lens radius 0.2 * height on the 1|2 interface, sigma_12 =
+    0.01, sigma_13 and sigma_23 uniform in [0.005, 0.015]; the first half run
+    Model B, the second half Model A with its exponent swept over
+    MODEL_A_SWEEP (equal shares).  Returns a list of (params, phi0)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    half = count // 2
+    for k in range(count):
+        nx, ny = sizes[int(rng.integers(len(sizes)))]
+        s13, s23 = (float(v) for v in rng.uniform(0.005, 0.015, 2))
+        if k < half:
+            model, n = "B", 1.0
+        else:
+            model, n = "A", MODEL_A_SWEEP[(k - half) * len(MODEL_A_SWEEP) // max(count - half, 1)]
+        out.append(lens(nx, ny, 0.2 * ny, 0.01, s13, s23, model=model, model_a_n=n))
+    return out

@@ -213,3 +213,25 @@ def test_store16_noise_model(oracle_built):
     plain.step(3)
     d0 = np.abs(plain.moments()[0] - ref.moments()[0]).max()
     assert d[1] > d[2] > d0
+
+
+def test_lens_reaches_neumann_equilibrium(oracle_built):
+    """A three-phase lens (phase 3) on the 1|2 interface between no-flux
+    walls, equal tensions (Table 3 case (c)): after 4000 steps the cap
+    heights are within 3% and the half-length within 6% of the closed form
+    of Sec. 4.3 for the measured lens area (160 x 80, R = 16, eps = 4: the
+    diffuse triple junction shortens the measured chord).  With a cheaper
+    lower interface the lower cap is the deeper one."""
+    from oracle.oracle import lens_equilibrium, measure_lens
+    p, phi0 = W.lens(160, 80, 16.0, 0.01, 0.01, 0.01, model="B")
+    o = OracleSim(p, phi0)
+    o.step(4000)
+    hd, hlo, hup, S = measure_lens(o.moments()[0])
+    ad, alo, aup, _, _ = lens_equilibrium(0.01, 0.01, 0.01, S)
+    assert abs(hlo / alo - 1) < 0.03 and abs(hup / aup - 1) < 0.03, (hlo, hup, alo)
+    assert abs(hd / ad - 1) < 0.06, (hd, ad)
+    p, phi0 = W.lens(160, 80, 16.0, 0.01, 0.006, 0.012, model="B")
+    o = OracleSim(p, phi0)
+    o.step(2000)
+    _, hlo, hup, _ = measure_lens(o.moments()[0])
+    assert hlo > 1.2 * hup

@@ -245,3 +245,23 @@ def test_chemical_potential_is_bulk_free_energy_derivative(oracle_built):
             e1[a] += h
             e2[a] -= h
             assert abs((E(e1) - E(e2)) / (2 * h) - mu[a]) < 1e-9
+
+
+def test_lens_closed_form_reproduces_table3():
+    """The Neumann closed form (Sec. 4.3, Eq. (33)) gives the analytical
+    columns of Table 3 (tests/golden/lens_table3_analytic.txt) for S = pi R^2,
+    R = 1: layer tension sigma_13 = 0.01, caps sigma_23 (h_1) and sigma_12
+    (h_2)."""
+    import os
+    from oracle.oracle import lens_equilibrium
+    path = os.path.join(os.path.dirname(__file__), "golden", "lens_table3_analytic.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 4
+    for case, s12, s23, d, h1, h2 in rows:
+        hd, ha, hb, _, _ = lens_equilibrium(0.01, float(s23), float(s12), np.pi)
+        assert abs(hd - float(d)) < 6e-5, case
+        assert abs(ha - float(h1)) < 6e-5, case
+        assert abs(hb - float(h2)) < 6e-5, case
+    # symmetric tensions: 60 degree caps, equal heights
+    hd, ha, hb, ta, tb = lens_equilibrium(1.0, 1.0, 1.0, 3.0)
+    assert abs(ta - np.pi / 3) < 1e-12 and abs(ha - hb) < 1e-12
