@@ -244,6 +244,8 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
             phi, u = (t.cpu().numpy() for t in sim.moments()[:2])
             m1 = sim.phase_mass(allow_diverged=True)
             sim.close()
+            del sim
+            torch.cuda.empty_cache()
             bpl = bytes_per_lup(N, st)
             fphi, fu = ref_fields
             forms[st] = {
@@ -293,6 +295,28 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
             "mass_drift_rel_max": drift,
         }
     return forms
+
+
+def run_forms_only(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2306_06983_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.lattice:
+        lx, ly = args.lattice
+        p, phi0 = W.random_disks(lx, ly, 5, max(1, int(round(200 * lx * ly / 2048 ** 2))), 10.0, 40.0,
+                                 model=args.model)
+    else:
+        p, phi0 = W.disks_2048(args.model)
+    N = p["n_phases"]
+    shape = (N, p["ny"], p["nx"])
+    ref = [np.zeros(shape, np.float32), np.zeros((2,) + shape[1:], np.float32)]
+    peak, _ = peak_hbm()
+    forms = measure_forms(args, p, phi0, ref, p["nx"] * p["ny"], peak)
+    for f in forms.values():
+        f.pop("vs_f32_after_same_steps", None)
+    print(json.dumps({"metric": METRIC, "forms": forms}), flush=True)
 
 
 def run_gpu(args):
@@ -452,11 +476,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the 16-bit storage and ensemble forms measured beside the headline")
+    ap.add_argument("--only-forms", action="store_true",
+                    help="profiling aid: time only the forms (on --lattice if given), print them")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_forms:
+        run_forms_only(args)
     else:
         run_gpu(args)
 
