@@ -294,7 +294,71 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
             "one_launch_per_member_mlups": round(nodes / ms1 / 1e3, 2),
             "mass_drift_rel_max": drift,
         }
+        del sims
+        torch.cuda.empty_cache()
+        forms["adjoint"] = measure_adjoint(timed)
     return forms
+
+
+def measure_adjoint(timed):
+    """Gradient study (256x256 periodic, N = 3, Model B, 500 steps, a
+    checkpoint every 50, smooth unit vectors delta = 1e-3): L = 1/2 |phi(T) -
+    phi_hat|^2 with phi_hat from sigma = (0.012, 0.008, 0.010); gradients with
+    respect to the three tensions, the mobility and the initial fields from
+    sigma = (0.01, 0.01, 0.01).  Forward (with checkpoints) and reverse sweep
+    timed with CUDA events; a plain forward of the same steps beside them."""
+    import torch
+    from paper_2306_06983_gb300 import workloads as W
+    from paper_2306_06983_gb300.nlbm import AdjointRun, Simulation, pair_list
+    T, every = 500, 50
+    p, phi0 = W.adjoint_problem(256, 256)
+    phi0 = phi0.astype(np.float32)
+    N = p["n_phases"]
+
+    def sig(s):
+        m = np.zeros((N, N))
+        for (a, b), v in zip(pair_list(N), s):
+            m[a, b] = m[b, a] = v
+        return m.tolist()
+    stream = torch.cuda.current_stream()
+    ref = Simulation(dict(p, sigma=sig((0.012, 0.008, 0.010))))
+    ref.set_phi(phi0)
+    ref.step(T)
+    tgt = ref.moments()[0]
+    ref.close()
+    q = dict(p, sigma=sig((0.01, 0.01, 0.01)))
+    plain = Simulation(q)
+    plain.set_phi(phi0)
+    plain.step(3)
+    ms_plain = timed(stream, plain.step, T) * T
+    plain.close()
+    run = AdjointRun(q, T, every)
+    run.forward(phi0)   # warm-up of both sweeps
+    run.backward(torch.zeros((N,) + phi0.shape[1:], device="cuda"))
+    l0 = run.kernel_launches
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    phiT = run.forward(phi0)
+    e[1].record(stream)
+    seed = (phiT - tgt).contiguous()
+    g0, gs, gm = run.backward(seed)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    launches = run.kernel_launches - l0
+    run.close()
+    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    nodes = 256 * 256
+    return {
+        "workload": "256x256 periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
+                    "v/sqrt(|v|^2+1e-6); L2 mismatch of phi(T) against the sigma=(0.012,0.008,0.010) run",
+        "value": round(nodes * T / ((fwd + bwd) / 1e3) / 1e6, 2), "unit": "MLUPS (differentiated)",
+        "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3), "backward_over_forward": round(bwd / fwd, 2),
+        "plain_forward_ms": round(ms_plain, 3), "gpu_launches": launches,
+        "loss": float(0.5 * ((phiT.double() - tgt.double()) ** 2).sum()),
+        "grad_sigma_pairs": [float(gs[a, b]) for a, b in pair_list(N)], "grad_mobility": float(gm),
+        "grad_phi0_max_abs": float(g0.abs().max()),
+    }
 
 
 def run_forms_only(args):

@@ -84,6 +84,12 @@ typedef struct nlbm_params {
     double gx, gy;         /* body acceleration; must be 0 (else ENOTSUP) */
     int32_t storage;       /* nlbm_storage */
     int32_t reserved;      /* must be 0 */
+    double unit_delta;     /* >= 0.  Unit vectors of the sources (n_p of
+                              Eq. (2), n_pq of Eq. (3)): 0 reads v/|v| as 0
+                              when |v|^2 <= 1e-24 (the paper leaves v = 0
+                              open); > 0 uses the smooth v / sqrt(|v|^2 +
+                              delta^2), which is what a differentiated run
+                              needs (see nlbm_adjoint_create) */
 } nlbm_params;
 
 typedef struct nlbm_sim nlbm_sim;

@@ -98,6 +98,8 @@ typedef struct {
     double rho[MAXN];
     double mu[MAXN];    /* dynamic viscosities */
     double sigma[MAXN * MAXN];
+    double unit_delta;  /* 0: unit vectors read as 0 when |v|^2 <= 1e-24; > 0: the
+                           smooth reading v / sqrt(|v|^2 + delta^2) */
 } or_params;
 
 typedef struct {
@@ -203,10 +205,14 @@ static real lap_at(const or_sim *s, const real *F, int x, int y)
 }
 
 /* Unit vector with the zero-gradient reading: 0 when |v|^2 <= 1e-24. */
-static void unit(real vx, real vy, real *nx, real *ny)
+static void unit(real vx, real vy, real delta, real *nx, real *ny)
 {
     real n2 = vx * vx + vy * vy;
-    if (n2 > 1e-24) {
+    if (delta > 0) {
+        real r = RSQRT_(n2 + delta * delta);
+        *nx = vx / r;
+        *ny = vy / r;
+    } else if (n2 > 1e-24) {
         real r = RSQRT_(n2);
         *nx = vx / r;
         *ny = vy / r;
@@ -350,7 +356,7 @@ static void source_at(const or_params *pp, int N, const real *phi, const real (*
         real sumw = 0, Vx = 0, Vy = 0, a[MAXN], nvx[MAXN], nvy[MAXN], w[MAXN];
         for (int q = 0; q < N; q++) {
             a[q] = 4.0 * phi[q] * (1.0 - phi[q]) / eps;
-            unit(gp[q][0], gp[q][1], &nvx[q], &nvy[q]);
+            unit(gp[q][0], gp[q][1], (real)pp->unit_delta, &nvx[q], &nvy[q]);
             w[q] = RPOW_(phi[q] > 0 ? phi[q] : (real)0, (real)pp->model_a_n);
             sumw += w[q];
             Vx += a[q] * nvx[q];
@@ -371,7 +377,7 @@ static void source_at(const or_params *pp, int N, const real *phi, const real (*
                 real vx = phi[q] * gp[p][0] - phi[p] * gp[q][0];
                 real vy = phi[q] * gp[p][1] - phi[p] * gp[q][1];
                 real ux, uy;
-                unit(vx, vy, &ux, &uy);
+                unit(vx, vy, (real)pp->unit_delta, &ux, &uy);
                 real c = 4.0 * phi[p] * phi[q] / eps;
                 rx += c * ux;
                 ry += c * uy;
@@ -394,6 +400,7 @@ static int valid(const or_params *p)
     if (p->nx < 1 || p->ny < 1 || p->n_phases < 2 || p->n_phases > MAXN) return 0;
     if ((p->wall_x && p->nx < 4) || (p->wall_y && p->ny < 4)) return 0;
     if (!(p->eps > 0) || !(p->mobility > 0)) return 0;
+    if (!(p->unit_delta >= 0) || !isfinite(p->unit_delta)) return 0;
     if (p->model != 0 && p->model != 1) return 0;
     if (p->model == 0 && !(p->model_a_n > 0)) return 0;
     for (int a = 0; a < p->n_phases; a++) {

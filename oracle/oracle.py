@@ -40,6 +40,7 @@ class params_struct(ctypes.Structure):
         ("mobility", ctypes.c_double),
         ("rho", ctypes.c_double * MAXN), ("mu", ctypes.c_double * MAXN),
         ("sigma", ctypes.c_double * (MAXN * MAXN)),
+        ("unit_delta", ctypes.c_double),
     ]
 
 
@@ -125,6 +126,7 @@ def make_params(p: dict, solve_all: bool = False, store16: int = 0) -> params_st
     s.solve_all = int(bool(solve_all))
     s.model_a_n = float(p.get("model_a_n", 1.0))
     s.eps, s.mobility = float(p["eps"]), float(p["mobility"])
+    s.unit_delta = float(p.get("unit_delta", 0.0))
     sig = np.asarray(p["sigma"], dtype=np.float64).reshape(N, N)
     for a in range(N):
         s.rho[a] = float(p["rho"][a])

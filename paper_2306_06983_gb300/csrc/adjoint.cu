@@ -1,0 +1,731 @@
+// Reverse (adjoint) of the fused step, Model B, periodic lattice, FP32.
+//
+// For a loss L(phi(T)) the adjoint runs the steps backwards.  For each step t
+// it first rebuilds the step's intermediate fields from the step's input
+// state (the "tape": phi, j, the pulled g, grad phi, lap phi, R, m_phi, w and
+// F, three per-node passes), then takes the adjoint through the step in four
+// per-node passes, each the transpose of a forward stage:
+//   rev1  pointwise at x: both collisions (Eqs. (18)-(24)), the macroscopic
+//         relations (Eqs. (25b), (25c), (13)), the mixture rules (Eqs. (11),
+//         (12)) and F_s with the chemical potentials (Eqs. (16), (17));
+//   rev2  transpose of F_c's stencil (gather of the F adjoint), then w,
+//         m_phi (Eq. (13)) and the Model B source (Eqs. (3), (4)) pointwise;
+//   rev3  transposes of the isotropic gradient and Laplacian (Eq. (27));
+//   rev4  transpose of the pull (streaming) and of the moments
+//         phi = sum f_i, j = sum c_i f_i (Eq. (25a)).
+// The adjoint of the step's inputs is the seed of the previous step.  The
+// derivatives are those of the exact-arithmetic step; the exact-sum devices
+// of the forward kernel (compensated sums, paired populations) change only
+// rounding.  Per-node contributions to dL/d sigma_pq and dL/dM are summed
+// in FP64 in a fixed order each step.
+#include "nlbm_internal.cuh"
+#include "adjoint.cuh"
+
+namespace nlbm {
+
+namespace {
+
+__constant__ int aCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int aCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+__device__ __forceinline__ float wgt(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
+
+__device__ __forceinline__ unsigned wrap_node(int x, int y, int nx, int ny)
+{
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    return (unsigned)y * nx + x;
+}
+
+// g'(s) = 2 s (1 - s) (1 - 2 s) and its derivative (Eq. (17)).
+__device__ __forceinline__ float gp1(float s) { return 2.f * s * (1.f - s) * (1.f - 2.f * s); }
+__device__ __forceinline__ float gp2(float s) { return 2.f - 12.f * s + 12.f * s * s; }
+
+// ------------------------------------------------------------------ tape
+
+// Pull and moments: phi_p, j_p (Eq. (25a)) and the pulled flow populations.
+template <int NS>
+__global__ void tape_pull_kernel(const StepParams P, AdjTape T)
+{
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            float ph = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float f = P.fin[((size_t)p * 9 + i) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
+                ph += f;
+                jx += aCx[i] * f;
+                jy += aCy[i] * f;
+            }
+            T.phi[(size_t)p * pl + k] = ph;
+            T.j[(size_t)(2 * p) * pl + k] = jx;
+            T.j[(size_t)(2 * p + 1) * pl + k] = jy;
+        }
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            T.g[(size_t)(i - 1) * pl + k] = P.gin[(size_t)(i - 1) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
+    }
+}
+
+// grad phi and lap phi (Eq. (27)) of phases 1..N-1, the Model B source
+// (Eqs. (3), (4)), m_phi (Eq. (13)) and w = m_phi,x u_y - u_x m_phi,y with
+// the previous velocity.
+template <int NS>
+__global__ void tape_stencil_kernel(const StepParams P, AdjTape T)
+{
+    constexpr int N = NS + 1;
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+        float ph[N], gx[N], gy[N];
+        float sph = 0.f, sgx = 0.f, sgy = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            const float *f = T.phi + (size_t)p * pl;
+            const float c = f[k];
+            float ax = 0.f, ay = 0.f, lap = 0.f;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const float v = f[wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny)];
+                ax += 3.f * wgt(i) * aCx[i] * v;
+                ay += 3.f * wgt(i) * aCy[i] * v;
+                lap += 6.f * wgt(i) * (v - c);
+            }
+            ph[p] = c;
+            gx[p] = ax;
+            gy[p] = ay;
+            T.grad[(size_t)(2 * p) * pl + k] = ax;
+            T.grad[(size_t)(2 * p + 1) * pl + k] = ay;
+            T.lap[(size_t)p * pl + k] = lap;
+            sph += c;
+            sgx += ax;
+            sgy += ay;
+        }
+        ph[NS] = 1.f - sph;
+        gx[NS] = -sgx;
+        gy[NS] = -sgy;
+        float Rx[NS], Ry[NS];
+#pragma unroll
+        for (int p = 0; p < NS; ++p) Rx[p] = Ry[p] = 0.f;
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                const float vx = ph[q] * gx[p] - ph[p] * gx[q], vy = ph[q] * gy[p] - ph[p] * gy[q];
+                const float n2 = vx * vx + vy * vy;
+                const float r = P.unit_delta2 > 0.f ? rsqrtf(n2 + P.unit_delta2) : (n2 > 1e-24f ? rsqrtf(n2) : 0.f);
+                const float c = P.four_over_eps * ph[p] * ph[q] * r;
+                if (p < NS) { Rx[p] += c * vx; Ry[p] += c * vy; }
+                if (q < NS) { Rx[q] -= c * vx; Ry[q] -= c * vy; }
+            }
+        float mx = 0.f, my = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            T.R[(size_t)(2 * p) * pl + k] = Rx[p];
+            T.R[(size_t)(2 * p + 1) * pl + k] = Ry[p];
+            mx += P.drho[p] * (gx[p] - Rx[p]);
+            my += P.drho[p] * (gy[p] - Ry[p]);
+        }
+        mx *= -P.mob;
+        my *= -P.mob;
+        T.mphi[k] = mx;
+        T.mphi[pl + k] = my;
+        T.w[k] = mx * P.uin[pl + k] - P.uin[k] * my;
+    }
+}
+
+// Chemical potentials of all N phases at one node (Eq. (17)).
+template <int NS>
+__device__ __forceinline__ void chem_pot(const StepParams &P, const float (&ph)[NS + 1], const float (&lap)[NS + 1],
+                                         float (&mu)[NS + 1])
+{
+    constexpr int N = NS + 1;
+    float g[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        g[p] = gp1(ph[p]);
+        mu[p] = 0.f;
+    }
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+        for (int q = p + 1; q < N; ++q) {
+            const float G = gp1(ph[p] + ph[q]);
+            mu[p] += P.beta2[p][q] * (g[p] - G) + P.kap[p][q] * lap[q];
+            mu[q] += P.beta2[p][q] * (g[q] - G) + P.kap[p][q] * lap[p];
+        }
+}
+
+// F = F_s + F_c (Eq. (16) and the lagged-velocity F_c).
+template <int NS>
+__global__ void tape_force_kernel(const StepParams P, AdjTape T)
+{
+    constexpr int N = NS + 1;
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+        float ph[N], lap[N], mu[N];
+        float sph = 0.f, sl = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            ph[p] = T.phi[(size_t)p * pl + k];
+            lap[p] = T.lap[(size_t)p * pl + k];
+            sph += ph[p];
+            sl += lap[p];
+        }
+        ph[NS] = 1.f - sph;
+        lap[NS] = -sl;
+        chem_pot<NS>(P, ph, lap, mu);
+        float Fx = 0.f, Fy = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            const float d = mu[p] - mu[NS];
+            Fx += d * T.grad[(size_t)(2 * p) * pl + k];
+            Fy += d * T.grad[(size_t)(2 * p + 1) * pl + k];
+        }
+        float dxw = 0.f, dyw = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float v = T.w[wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny)];
+            dxw += 3.f * wgt(i) * aCx[i] * v;
+            dyw += 3.f * wgt(i) * aCy[i] * v;
+        }
+        T.F[k] = Fx + 0.5f * dyw;
+        T.F[pl + k] = Fy - 0.5f * dxw;
+    }
+}
+
+// ---------------------------------------------------------------- reverse
+
+// rev1: pointwise adjoint of the collisions and everything between the
+// tape fields and them.  Seeds at x: A.lf_out (f*), A.lg_out (g*), A.lphi_out
+// (phi(t): the next step's phi_prev and the loss), A.lu_out, A.lm_out.
+template <int NS>
+__global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
+{
+    constexpr int N = NS + 1;
+    constexpr int NP = N * (N - 1) / 2;
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        // ---------------- forward values at x
+        float ph[N], lap[N], gx[NS], gy[NS], jx[NS], jy[NS], Rx[NS], Ry[NS], php[NS];
+        float sph = 0.f, sl = 0.f, rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f, rho_prev = P.rhoN;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            ph[p] = T.phi[(size_t)p * pl + k];
+            lap[p] = T.lap[(size_t)p * pl + k];
+            gx[p] = T.grad[(size_t)(2 * p) * pl + k];
+            gy[p] = T.grad[(size_t)(2 * p + 1) * pl + k];
+            jx[p] = T.j[(size_t)(2 * p) * pl + k];
+            jy[p] = T.j[(size_t)(2 * p + 1) * pl + k];
+            Rx[p] = T.R[(size_t)(2 * p) * pl + k];
+            Ry[p] = T.R[(size_t)(2 * p + 1) * pl + k];
+            php[p] = P.phi_prev[(size_t)p * pl + k];
+            sph += ph[p];
+            sl += lap[p];
+            rho += P.drho[p] * ph[p];
+            mu += P.dmu[p] * ph[p];
+            grx += P.drho[p] * gx[p];
+            gry += P.drho[p] * gy[p];
+            rho_prev += P.drho[p] * php[p];
+        }
+        ph[NS] = 1.f - sph;
+        lap[NS] = -sl;
+        float g[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) g[i] = T.g[(size_t)(i - 1) * pl + k];
+        const float Fx = T.F[k], Fy = T.F[pl + k];
+        const float mphx = T.mphi[k], mphy = T.mphi[pl + k];
+        const float upx = P.uin[k], upy = P.uin[pl + k];
+        const float mpx = P.mphi[k], mpy = P.mphi[pl + k];   // m_phi of step t-1
+        const float sg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+        const float jgx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+        const float jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+        const float d58 = (g[5] + g[6]) + (g[7] + g[8]);
+        const float Pxx = (g[1] + g[3]) + d58, Pyy = (g[2] + g[4]) + d58, Pxy = (g[5] - g[6]) + (g[7] - g[8]);
+        const float ux = (jgx + 0.5f * Fx) / rho, uy = (jgy + 0.5f * Fy) / rho;
+        const float mx = rho * ux + mphx, my = rho * uy + mphy;
+        const float ugr = ux * grx + uy * gry;
+        const float mu_t = mx * ux + my * uy;
+        const float mu_prev = (rho_prev * upx + mpx) * upx + (rho_prev * upy + mpy) * upy;
+        const float Pr = 0.6f * (sg + 0.5f * ugr - (1.f / 3.f) * mu_t - (1.f / 3.f) * mu_prev);
+        const float den = 6.f * mu + rho;
+        const float s2 = 2.f * rho / den, c2 = 1.f - s2, h2 = 1.f - 0.5f * s2;
+        const float Qxx = mx * ux, Qyy = my * uy, Qxy = 0.5f * (mx * uy + my * ux);
+        const float dQxx = mphx * ux - mpx * upx, dQyy = mphy * uy - mpy * upy;
+        const float dQxy = 0.5f * ((mphx * uy + mphy * ux) - (mpx * upy + mpy * upx));
+        const float Mxx = 2.f * ux * Fx + dQxx + (2.f / 3.f) * ux * grx + (1.f / 3.f) * ugr;
+        const float Myy = 2.f * uy * Fy + dQyy + (2.f / 3.f) * uy * gry + (1.f / 3.f) * ugr;
+        const float Mxy = ux * Fy + Fx * uy + dQxy + (1.f / 3.f) * (ux * gry + grx * uy);
+
+        // ---------------- adjoint accumulators
+        float a_ph[N], a_lap[N], a_gx[NS], a_gy[NS], a_Rx[NS], a_Ry[NS], a_php[NS];
+#pragma unroll
+        for (int p = 0; p < N; ++p) { a_ph[p] = 0.f; a_lap[p] = 0.f; }
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            a_ph[p] = A.lphi_out[(size_t)p * pl + k];
+            a_gx[p] = a_gy[p] = a_Rx[p] = a_Ry[p] = a_php[p] = 0.f;
+        }
+        float a_ux = A.lu_out[k], a_uy = A.lu_out[pl + k];
+        float a_mphx = A.lm_out[k], a_mphy = A.lm_out[pl + k];
+        float a_upx = 0.f, a_upy = 0.f, a_mpx = 0.f, a_mpy = 0.f;
+        float a_Fx = 0.f, a_Fy = 0.f, a_rho = 0.f, a_mu = 0.f, a_grx = 0.f, a_gry = 0.f, a_s1 = 0.f;
+
+        // ---------------- flow collision (Eqs. (21)-(24)) reversed
+        float lg[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) lg[i] = A.lg_out[(size_t)(i - 1) * pl + k];
+        const float a_m1 = 0.5f * (lg[1] - lg[3]);
+        const float a_m2 = 0.5f * (lg[2] - lg[4]);
+        const float a_m3 = 0.5f * (lg[1] + lg[3]);
+        const float a_m4 = 0.5f * (lg[2] + lg[4]);
+        const float a_m5 = 0.25f * ((lg[5] - lg[6]) + (lg[7] - lg[8]));
+        const float a_m6 = -0.5f * (lg[2] - lg[4]) + 0.25f * ((lg[5] + lg[6]) - (lg[7] + lg[8]));
+        const float a_m7 = -0.5f * (lg[1] - lg[3]) + 0.25f * ((lg[5] - lg[6]) - (lg[7] - lg[8]));
+        const float a_m8 = -0.5f * ((lg[1] + lg[2]) + (lg[3] + lg[4])) + 0.25f * ((lg[5] + lg[6]) + (lg[7] + lg[8]));
+        // m8 = (P + Qxx + Qyy)/3 + (Mxx + Myy)/6 - ugr/18
+        float a_P = a_m8 / 3.f, a_Qxx = a_m8 / 3.f, a_Qyy = a_m8 / 3.f;
+        float a_Mxx = a_m8 / 6.f, a_Myy = a_m8 / 6.f, a_ugr = -a_m8 / 18.f;
+        // m7 = rho ux/3 + Fx/6, m6 = rho uy/3 + Fy/6
+        a_rho += (a_m7 * ux + a_m6 * uy) / 3.f;
+        a_ux += a_m7 * rho / 3.f;
+        a_uy += a_m6 * rho / 3.f;
+        a_Fx += a_m7 / 6.f;
+        a_Fy += a_m6 / 6.f;
+        // m5 = c2 Pxy + s2 Qxy + h2 Mxy; m4, m3 likewise
+        float a_Pxy = c2 * a_m5, a_Qxy = s2 * a_m5, a_Mxy = h2 * a_m5;
+        float a_s2 = (-Pxy + Qxy - 0.5f * Mxy) * a_m5;
+        float a_Pyy = c2 * a_m4;
+        a_P += s2 * a_m4;
+        a_Qyy += s2 * a_m4;
+        a_Myy += h2 * a_m4;
+        a_s2 += (-Pyy + Pr + Qyy - 0.5f * Myy) * a_m4;
+        float a_Pxx = c2 * a_m3;
+        a_P += s2 * a_m3;
+        a_Qxx += s2 * a_m3;
+        a_Mxx += h2 * a_m3;
+        a_s2 += (-Pxx + Pr + Qxx - 0.5f * Mxx) * a_m3;
+        // m1 = jgx + Fx, m2 = jgy + Fy
+        float a_jgx = a_m1, a_jgy = a_m2;
+        a_Fx += a_m1;
+        a_Fy += a_m2;
+        // Mxy, Myy, Mxx
+        a_ux += a_Mxy * (Fy + gry / 3.f);
+        a_uy += a_Mxy * (Fx + grx / 3.f);
+        a_Fx += a_Mxy * uy;
+        a_Fy += a_Mxy * ux;
+        a_grx += a_Mxy * uy / 3.f;
+        a_gry += a_Mxy * ux / 3.f;
+        float a_dQxy = a_Mxy;
+        a_uy += a_Myy * (2.f * Fy + (2.f / 3.f) * gry);
+        a_Fy += 2.f * uy * a_Myy;
+        a_gry += (2.f / 3.f) * uy * a_Myy;
+        a_ugr += a_Myy / 3.f;
+        float a_dQyy = a_Myy;
+        a_ux += a_Mxx * (2.f * Fx + (2.f / 3.f) * grx);
+        a_Fx += 2.f * ux * a_Mxx;
+        a_grx += (2.f / 3.f) * ux * a_Mxx;
+        a_ugr += a_Mxx / 3.f;
+        float a_dQxx = a_Mxx;
+        // dQ terms
+        a_mphx += 0.5f * uy * a_dQxy + ux * a_dQxx;
+        a_mphy += 0.5f * ux * a_dQxy + uy * a_dQyy;
+        a_ux += 0.5f * mphy * a_dQxy + mphx * a_dQxx;
+        a_uy += 0.5f * mphx * a_dQxy + mphy * a_dQyy;
+        a_mpx -= 0.5f * upy * a_dQxy + upx * a_dQxx;
+        a_mpy -= 0.5f * upx * a_dQxy + upy * a_dQyy;
+        a_upx -= 0.5f * mpy * a_dQxy + mpx * a_dQxx;
+        a_upy -= 0.5f * mpx * a_dQxy + mpy * a_dQyy;
+        // Q terms: Qxx = mx ux, Qyy = my uy, Qxy = (mx uy + my ux)/2
+        float a_mx = ux * a_Qxx + 0.5f * uy * a_Qxy;
+        float a_my = uy * a_Qyy + 0.5f * ux * a_Qxy;
+        a_ux += mx * a_Qxx + 0.5f * my * a_Qxy;
+        a_uy += my * a_Qyy + 0.5f * mx * a_Qxy;
+        // s2 = 2 rho / (6 mu + rho)
+        a_rho += a_s2 * 12.f * mu / (den * den);
+        a_mu += -a_s2 * 12.f * rho / (den * den);
+        // ---------------- phase collisions (Eqs. (18)-(20)) reversed
+        const float s1 = P.s1, h1 = (1.f - 0.5f * s1) / 3.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            float lf[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) lf[i] = A.lf_out[((size_t)p * 9 + i) * pl + k];
+            const float phi = ph[p];
+            const float Gx = 3.f * (phi * ux - php[p] * upx) + Rx[p];
+            const float Gy = 3.f * (phi * uy - php[p] * upy) + Ry[p];
+            float a_phi = (4.f / 9.f) * lf[0] + ((lf[1] + lf[2]) + (lf[3] + lf[4])) / 9.f +
+                          ((lf[5] + lf[6]) + (lf[7] + lf[8])) / 36.f;
+            const float a_A = 0.5f * (lf[1] - lf[3]), a_B = 0.5f * (lf[2] - lf[4]);
+            const float a_C = -0.5f * (lf[2] - lf[4]) + 0.25f * ((lf[5] - lf[7]) + (lf[6] - lf[8]));
+            const float a_D = -0.5f * (lf[1] - lf[3]) + 0.25f * ((lf[5] - lf[7]) - (lf[6] - lf[8]));
+            // C = phi uy/3 + Gy/18, D = phi ux/3 + Gx/18
+            a_phi += (a_C * uy + a_D * ux) / 3.f;
+            a_uy += a_C * phi / 3.f;
+            a_ux += a_D * phi / 3.f;
+            float a_Gy = a_C / 18.f, a_Gx = a_D / 18.f;
+            // A = (1 - s1) jx + s1 phi ux + h1 Gx, B likewise
+            A.lj[(size_t)(2 * p) * pl + k] = (1.f - s1) * a_A;
+            A.lj[(size_t)(2 * p + 1) * pl + k] = (1.f - s1) * a_B;
+            a_phi += s1 * (ux * a_A + uy * a_B);
+            a_ux += s1 * phi * a_A;
+            a_uy += s1 * phi * a_B;
+            a_Gx += h1 * a_A;
+            a_Gy += h1 * a_B;
+            a_s1 += (-jx[p] + phi * ux - Gx / 6.f) * a_A + (-jy[p] + phi * uy - Gy / 6.f) * a_B;
+            // G = 3 (phi u - phi_prev u_prev) + R
+            a_phi += 3.f * (ux * a_Gx + uy * a_Gy);
+            a_ux += 3.f * phi * a_Gx;
+            a_uy += 3.f * phi * a_Gy;
+            a_php[p] -= 3.f * (upx * a_Gx + upy * a_Gy);
+            a_upx -= 3.f * php[p] * a_Gx;
+            a_upy -= 3.f * php[p] * a_Gy;
+            a_Rx[p] += a_Gx;
+            a_Ry[p] += a_Gy;
+            a_ph[p] += a_phi;
+        }
+
+        // ---------------- pressure (Eq. (25c)) and m (Eq. (13)) reversed
+        a_ugr += 0.3f * a_P;
+        const float a_mut = -0.2f * a_P, a_mup = -0.2f * a_P;
+        // mu_prev = (rho_prev up + mp) . up
+        const float a_rhop = a_mup * (upx * upx + upy * upy);
+        a_upx += a_mup * (2.f * rho_prev * upx + mpx);
+        a_upy += a_mup * (2.f * rho_prev * upy + mpy);
+        a_mpx += a_mup * upx;
+        a_mpy += a_mup * upy;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) a_php[p] += P.drho[p] * a_rhop;
+        // mu_t = m . u
+        a_mx += a_mut * ux;
+        a_my += a_mut * uy;
+        a_ux += a_mut * mx;
+        a_uy += a_mut * my;
+        // ugr = u . grad rho
+        a_ux += a_ugr * grx;
+        a_uy += a_ugr * gry;
+        a_grx += a_ugr * ux;
+        a_gry += a_ugr * uy;
+        // m = rho u + m_phi
+        a_rho += a_mx * ux + a_my * uy;
+        a_ux += rho * a_mx;
+        a_uy += rho * a_my;
+        a_mphx += a_mx;
+        a_mphy += a_my;
+        // u = (jg + F/2) / rho (Eq. (25b))
+        a_jgx += a_ux / rho;
+        a_jgy += a_uy / rho;
+        a_Fx += 0.5f * a_ux / rho;
+        a_Fy += 0.5f * a_uy / rho;
+        a_rho -= (a_ux * ux + a_uy * uy) / rho;
+        // sg, jg and Pi of the pulled flow populations (P = 0.6 (sg + ...))
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float cx = (float)aCx[i], cy = (float)aCy[i];
+            A.lg_pull[(size_t)(i - 1) * pl + k] = 0.6f * a_P + (cx * a_jgx + cy * a_jgy) + cx * cx * a_Pxx +
+                                                  cy * cy * a_Pyy + cx * cy * a_Pxy;
+        }
+
+        // ---------------- mixture rules (Eqs. (11), (12)) and F_s (Eqs. (16), (17))
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            a_ph[p] += P.drho[p] * a_rho + P.dmu[p] * a_mu;
+            a_gx[p] += P.drho[p] * a_grx;
+            a_gy[p] += P.drho[p] * a_gry;
+        }
+        float mu_c[N];
+        chem_pot<NS>(P, ph, lap, mu_c);
+        float a_muc[N];
+        a_muc[NS] = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            a_muc[p] = a_Fx * gx[p] + a_Fy * gy[p];
+            a_muc[NS] -= a_muc[p];
+            const float d = mu_c[p] - mu_c[NS];
+            a_gx[p] += d * a_Fx;
+            a_gy[p] += d * a_Fy;
+        }
+        float dsig[NP > 0 ? NP : 1];
+        int pair = 0;
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                const float s = ph[p] + ph[q];
+                const float b = P.beta2[p][q], kq = P.kap[p][q];
+                const float G2 = gp2(s);
+                a_ph[p] += a_muc[p] * b * (gp2(ph[p]) - G2) - a_muc[q] * b * G2;
+                a_ph[q] += a_muc[q] * b * (gp2(ph[q]) - G2) - a_muc[p] * b * G2;
+                a_lap[q] += kq * a_muc[p];
+                a_lap[p] += kq * a_muc[q];
+                // beta2 = 6 sigma / eps, kap = 3 eps sigma / 4
+                const float G1 = gp1(s);
+                dsig[pair++] = a_muc[p] * (P.six_over_eps * (gp1(ph[p]) - G1) + P.three_eps_over_4 * lap[q]) +
+                               a_muc[q] * (P.six_over_eps * (gp1(ph[q]) - G1) + P.three_eps_over_4 * lap[p]);
+            }
+        // phase N = 1 - sum: fold its adjoints onto phases 1..N-1
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            a_ph[p] -= a_ph[NS];
+            a_lap[p] -= a_lap[NS];
+        }
+
+        // ---------------- outputs
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            A.lphi_pw[(size_t)p * pl + k] = a_ph[p];
+            A.llap[(size_t)p * pl + k] = a_lap[p];
+            A.lgrad[(size_t)(2 * p) * pl + k] = a_gx[p];
+            A.lgrad[(size_t)(2 * p + 1) * pl + k] = a_gy[p];
+            A.lR[(size_t)(2 * p) * pl + k] = a_Rx[p];
+            A.lR[(size_t)(2 * p + 1) * pl + k] = a_Ry[p];
+            A.lphi_in[(size_t)p * pl + k] = a_php[p];
+        }
+        A.lF[k] = a_Fx;
+        A.lF[pl + k] = a_Fy;
+        A.lmphi[k] = a_mphx;
+        A.lmphi[pl + k] = a_mphy;
+        A.lu_in[k] = a_upx;
+        A.lu_in[pl + k] = a_upy;
+        A.lm_in[k] = a_mpx;
+        A.lm_in[pl + k] = a_mpy;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) A.contrib[(size_t)q * pl + k] = dsig[q];
+        // s1 = 1 / (1/2 + 3 M): d s1 / dM = -3 s1^2
+        A.contrib[(size_t)NP * pl + k] = -3.f * s1 * s1 * a_s1;
+    }
+}
+
+// rev2: F_c's stencil transposed (gather of the F adjoint at the
+// neighbours), then w, m_phi and the Model B source at the node.
+template <int NS>
+__global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
+{
+    constexpr int N = NS + 1;
+    constexpr int NP = N * (N - 1) / 2;
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+        // F_c(x) = (1/2 d_y w, -1/2 d_x w): w(z) enters F_c(z - c_i) with
+        // weight 3 w_i c_i.
+        float a_w = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
+            a_w += 3.f * wgt(i) * (0.5f * aCy[i] * A.lF[n] - 0.5f * aCx[i] * A.lF[pl + n]);
+        }
+        const float upx = P.uin[k], upy = P.uin[pl + k];
+        const float mphx = T.mphi[k], mphy = T.mphi[pl + k];
+        // w = mx uy - ux my (previous velocity)
+        const float a_mx = A.lmphi[k] + a_w * upy;
+        const float a_my = A.lmphi[pl + k] - a_w * upx;
+        A.lu_in[k] += -a_w * mphy;
+        A.lu_in[pl + k] += a_w * mphx;
+        // m_phi = -M sum_p drho_p (grad phi_p - R_p)
+        float ph[N], gx[N], gy[N], a_ph[N], a_gx[N], a_gy[N], a_Rx[NS], a_Ry[NS];
+        float sph = 0.f, sgx = 0.f, sgy = 0.f, dM = 0.f;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            ph[p] = T.phi[(size_t)p * pl + k];
+            gx[p] = T.grad[(size_t)(2 * p) * pl + k];
+            gy[p] = T.grad[(size_t)(2 * p + 1) * pl + k];
+            sph += ph[p];
+            sgx += gx[p];
+            sgy += gy[p];
+            a_ph[p] = 0.f;
+            a_gx[p] = A.lgrad[(size_t)(2 * p) * pl + k] - P.mob * P.drho[p] * a_mx;
+            a_gy[p] = A.lgrad[(size_t)(2 * p + 1) * pl + k] - P.mob * P.drho[p] * a_my;
+            a_Rx[p] = A.lR[(size_t)(2 * p) * pl + k] + P.mob * P.drho[p] * a_mx;
+            a_Ry[p] = A.lR[(size_t)(2 * p + 1) * pl + k] + P.mob * P.drho[p] * a_my;
+            const float Rx = T.R[(size_t)(2 * p) * pl + k], Ry = T.R[(size_t)(2 * p + 1) * pl + k];
+            dM -= P.drho[p] * ((gx[p] - Rx) * a_mx + (gy[p] - Ry) * a_my);
+        }
+        ph[NS] = 1.f - sph;
+        gx[NS] = -sgx;
+        gy[NS] = -sgy;
+        a_ph[NS] = a_gx[NS] = a_gy[NS] = 0.f;
+        // Model B source: pair (p, q) adds T = (4/eps) phi_p phi_q n_pq to R_p
+        // and subtracts it from R_q, n_pq = unit(phi_q grad phi_p - phi_p grad phi_q)
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                float apx = p < NS ? a_Rx[p] : 0.f, apy = p < NS ? a_Ry[p] : 0.f;
+                if (q < NS) { apx -= a_Rx[q]; apy -= a_Ry[q]; }
+                const float vx = ph[q] * gx[p] - ph[p] * gx[q], vy = ph[q] * gy[p] - ph[p] * gy[q];
+                const float n2 = vx * vx + vy * vy;
+                // n = v / s, s = sqrt(|v|^2 + delta^2) (or |v|; n = 0 below the threshold)
+                if (!(P.unit_delta2 > 0.f) && !(n2 > 1e-24f)) continue;
+                const float r = P.unit_delta2 > 0.f ? rsqrtf(n2 + P.unit_delta2) : rsqrtf(n2);
+                const float nx_ = vx * r, ny_ = vy * r;
+                const float c = P.four_over_eps;
+                const float an = apx * nx_ + apy * ny_;
+                a_ph[p] += c * ph[q] * an;
+                a_ph[q] += c * ph[p] * an;
+                const float anx = c * ph[p] * ph[q] * apx, any = c * ph[p] * ph[q] * apy;
+                const float dot = anx * nx_ + any * ny_;
+                const float avx = (anx - dot * nx_) * r, avy = (any - dot * ny_) * r;
+                a_ph[q] += avx * gx[p] + avy * gy[p];
+                a_gx[p] += ph[q] * avx;
+                a_gy[p] += ph[q] * avy;
+                a_ph[p] -= avx * gx[q] + avy * gy[q];
+                a_gx[q] -= ph[p] * avx;
+                a_gy[q] -= ph[p] * avy;
+            }
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            A.lphi_pw[(size_t)p * pl + k] += a_ph[p] - a_ph[NS];
+            A.lgrad[(size_t)(2 * p) * pl + k] = a_gx[p] - a_gx[NS];
+            A.lgrad[(size_t)(2 * p + 1) * pl + k] = a_gy[p] - a_gy[NS];
+        }
+        A.contrib[(size_t)NP * pl + k] += dM;
+    }
+}
+
+// rev3: the gradient and Laplacian stencils transposed: phi_p(z) entered
+// grad phi_p(z - c_i) with weight 3 w_i c_i and lap phi_p(z - c_i) with 6 w_i
+// (and lap phi_p(z) with -6 (1 - w_0)).
+template <int NS>
+__global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
+{
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+            const float *lgx = A.lgrad + (size_t)(2 * p) * pl, *lgy = A.lgrad + (size_t)(2 * p + 1) * pl;
+            const float *ll = A.llap + (size_t)p * pl;
+            float a = A.lphi_pw[(size_t)p * pl + k] - 6.f * (1.f - 4.f / 9.f) * ll[k];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
+                a += 3.f * wgt(i) * (aCx[i] * lgx[n] + aCy[i] * lgy[n]) + 6.f * wgt(i) * ll[n];
+            }
+            A.lphi_tot[(size_t)p * pl + k] = a;
+        }
+    }
+}
+
+// rev4: the pull and the moments transposed.  f_i(z) = f*_i(z - c_i) fed
+// phi(z) and j(z): the adjoint of f*_i at y is lphi(y + c_i) + c_i . lj(y + c_i);
+// likewise for the flow populations.  The results seed the previous step.
+template <int NS>
+__global__ void rev_pull_kernel(const StepParams P, AdjFields A)
+{
+    const unsigned pl = P.plane;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const int x = k % P.nx, y = k / P.nx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const unsigned n = wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny);
+#pragma unroll
+            for (int p = 0; p < NS; ++p)
+                A.lf_in[((size_t)p * 9 + i) * pl + k] = A.lphi_tot[(size_t)p * pl + n] +
+                                                        aCx[i] * A.lj[(size_t)(2 * p) * pl + n] +
+                                                        aCy[i] * A.lj[(size_t)(2 * p + 1) * pl + n];
+            if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = A.lg_pull[(size_t)(i - 1) * pl + n];
+        }
+    }
+}
+
+constexpr int kRedThreads = 256;
+
+// Fixed-order FP64 sums of K per-node fields, added to acc[K].
+__global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const float *__restrict__ contrib, int K,
+                                                                     unsigned n, double *partials)
+{
+    __shared__ double red[kRedThreads];
+    for (int c = 0; c < K; ++c) {
+        double v = 0.0;
+        for (unsigned k = blockIdx.x * kRedThreads + threadIdx.x; k < n; k += gridDim.x * kRedThreads)
+            v += (double)contrib[(size_t)c * n + k];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * K + c] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void reduce_final_kernel(const double *__restrict__ partials, int K, int nblocks, double *acc)
+{
+    const int c = threadIdx.x;
+    if (c >= K) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partials[(size_t)b * K + c];
+    acc[c] += v;
+}
+
+int blocks_for(unsigned n)
+{
+    unsigned b = (n + 255) / 256;
+    if (b > 152u * 16u) b = 152u * 16u;
+    return (int)(b ? b : 1);
+}
+
+template <int NS>
+cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, double *partials,
+                            double *acc, cudaStream_t st)
+{
+    constexpr int NP = (NS + 1) * NS / 2;
+    const int nb = blocks_for(P.plane);
+    tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+    tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+    tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+    rev_collide_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
+    rev_source_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
+    rev_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, A);
+    rev_pull_kernel<NS><<<nb, 256, 0, st>>>(P, A);
+    reduce_partial_kernel<<<kAdjRedBlocks, kRedThreads, 0, st>>>(A.contrib, NP + 1, P.plane, partials);
+    reduce_final_kernel<<<1, 64, 0, st>>>(partials, NP + 1, kAdjRedBlocks, acc);
+    return cudaGetLastError();
+}
+
+// dL/dphi_p for the solved phases from dL/dphi over all N phases (phi_N = 1 - sum).
+__global__ void fold_seed_kernel(int ns, const float *__restrict__ seed, unsigned pl, float *lphi)
+{
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+        const float last = seed[(size_t)ns * pl + k];
+        for (int p = 0; p < ns; ++p) lphi[(size_t)p * pl + k] = seed[(size_t)p * pl + k] - last;
+    }
+}
+
+__global__ void add_planes_kernel(const float *__restrict__ a, const float *__restrict__ b, unsigned n, float *out)
+{
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) out[k] = a[k] + b[k];
+}
+
+}  // namespace
+
+cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A,
+                                double *partials, double *acc, cudaStream_t st)
+{
+    switch (ns) {
+#define NLBM_CASE(K) \
+    case K: return reverse_step_ns<K>(P, T, A, partials, acc, st);
+        NLBM_CASE(1) NLBM_CASE(2) NLBM_CASE(3) NLBM_CASE(4) NLBM_CASE(5) NLBM_CASE(6) NLBM_CASE(7)
+#undef NLBM_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fold_seed(int ns, const float *seed, unsigned plane, float *lphi, cudaStream_t st)
+{
+    fold_seed_kernel<<<blocks_for(plane), 256, 0, st>>>(ns, seed, plane, lphi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_planes(const float *a, const float *b, unsigned n, float *out, cudaStream_t st)
+{
+    add_planes_kernel<<<blocks_for(n), 256, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nlbm

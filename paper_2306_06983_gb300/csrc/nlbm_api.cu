@@ -11,6 +11,7 @@
 
 #include "../../include/nlbm.h"
 #include "nlbm_internal.cuh"
+#include "adjoint.cuh"
 
 using namespace nlbm;
 
@@ -108,6 +109,7 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
         }
     }
     if (p->reserved != 0) { set_err(err, "reserved must be 0"); return NLBM_EINVAL; }
+    if (!std::isfinite(p->unit_delta) || p->unit_delta < 0.0) { set_err(err, "unit_delta must be >= 0"); return NLBM_EINVAL; }
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) { set_err(err, "gravity not finite"); return NLBM_EINVAL; }
     if (p->gx != 0.0 || p->gy != 0.0) { set_err(err, "gravity is not supported"); return NLBM_ENOTSUP; }
     if (p->storage != NLBM_STORE_F32 && !is_half(p->storage)) { set_err(err, "unknown storage"); return NLBM_EINVAL; }
@@ -136,6 +138,9 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
                 kp->kap[a][b] = (float)(0.75 * p->eps * s);        // -k_pq, Eq. (15)
             }
         kp->four_over_eps = (float)(4.0 / p->eps);
+        kp->unit_delta2 = (float)(p->unit_delta * p->unit_delta);
+        kp->six_over_eps = (float)(6.0 / p->eps);
+        kp->three_eps_over_4 = (float)(0.75 * p->eps);
         kp->mob = (float)p->mobility;
         kp->s1 = (float)(1.0 / (0.5 + 3.0 * p->mobility));        // Eq. (20), c_s^2 = 1/3
         kp->model_n = (float)p->model_a_n;
@@ -923,6 +928,366 @@ void nlbm_batch_destroy(nlbm_batch *b)
 }
 
 const char *nlbm_batch_last_error(const nlbm_batch *b) { return b ? b->err : g_err; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- adjoint
+
+struct nlbm_adjoint {
+    nlbm_sim *sim;             // forward simulation (its own workspace slice)
+    int ns, N, nsteps, every, nckpt;
+    size_t plane, state_floats;
+    cudaStream_t stream;
+    char *ws;
+    float *ckpt;               // [nckpt][state]
+    float *seg;                // [every][state]
+    AdjTape T;
+    float *seed[2];            // two sets of step-output adjoints
+    AdjFields A;               // intermediates (the seed pointers are set per step)
+    double *partials, *acc;    // [kAdjRedBlocks][NP+1], [NP+1]
+    bool forward_done;
+    char err[512];
+};
+
+namespace {
+
+// State of a simulation between steps: f [9 NS], g [8], u [2], phi [NS],
+// m_phi [2] planes (FP32 storage).
+size_t adj_state_floats(int ns, size_t plane) { return plane * ((size_t)ns * 9 + 8 + 2 + ns + 2); }
+
+// Offsets of the per-node arrays of the tape, the two seed sets and the
+// intermediates, in floats per plane.
+struct AdjCounts {
+    int tape, seedset, inter, contrib;
+};
+
+AdjCounts adj_counts(int ns)
+{
+    const int np = (ns + 1) * ns / 2;
+    return AdjCounts{8 * ns + 13, 10 * ns + 12, 9 * ns + 12, np + 1};
+}
+
+struct AdjLayout {
+    size_t sim, ckpt, seg, fields, partials, acc, total;
+};
+
+nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L, char *err)
+{
+    nlbm_status st = validate(p, nullptr, err);
+    if (st != NLBM_OK) return st;
+    if (p->model != NLBM_MODEL_B || p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC ||
+        p->storage != NLBM_STORE_F32) {
+        set_err(err, "the adjoint covers Model B on a periodic lattice with FP32 storage");
+        return NLBM_ENOTSUP;
+    }
+    if (nsteps < 1 || every < 1) { set_err(err, "nsteps and checkpoint interval must be >= 1"); return NLBM_EINVAL; }
+    const int ns = p->n_phases - 1;
+    const size_t plane = (size_t)p->nx * p->ny;
+    const int nckpt = (nsteps + every - 1) / every;
+    const AdjCounts c = adj_counts(ns);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L->sim = take(make_layout(ns, plane, false).total);
+    L->ckpt = take(sizeof(float) * adj_state_floats(ns, plane) * nckpt);
+    L->seg = take(sizeof(float) * adj_state_floats(ns, plane) * (size_t)(every < nsteps ? every : nsteps));
+    L->fields = take(sizeof(float) * plane * (size_t)(c.tape + 2 * c.seedset + c.inter + c.contrib));
+    L->partials = take(sizeof(double) * kAdjRedBlocks * c.contrib);
+    L->acc = take(sizeof(double) * c.contrib);
+    L->total = off;
+    return NLBM_OK;
+}
+
+nlbm_status adj_fail(nlbm_adjoint *a, cudaError_t e, const char *what)
+{
+    set_err(a->err, "%s: %s", what, cudaGetErrorString(e));
+    return NLBM_ECUDA;
+}
+
+// Copy the simulation's current state into / out of a packed state record.
+cudaError_t adj_save_state(nlbm_adjoint *a, float *dst)
+{
+    nlbm_sim *s = a->sim;
+    const size_t pl = a->plane, pb = sizeof(float) * pl;
+    const int c = s->cur;
+    struct Part { const void *src; size_t n; } parts[] = {
+        {s->f(c), pb * 9 * a->ns}, {s->g(c), pb * 8}, {s->u(c), pb * 2}, {s->phi(c), pb * a->ns}, {s->mphi(), pb * 2}};
+    char *d = (char *)dst;
+    for (const Part &p : parts) {
+        cudaError_t e = cudaMemcpyAsync(d, p.src, p.n, cudaMemcpyDeviceToDevice, a->stream);
+        if (e != cudaSuccess) return e;
+        d += p.n;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t adj_load_state(nlbm_adjoint *a, const float *src)
+{
+    nlbm_sim *s = a->sim;
+    const size_t pl = a->plane, pb = sizeof(float) * pl;
+    s->cur = 0;
+    struct Part { void *dst; size_t n; } parts[] = {
+        {s->f(0), pb * 9 * a->ns}, {s->g(0), pb * 8}, {s->u(0), pb * 2}, {s->phi(0), pb * a->ns}, {s->mphi(), pb * 2}};
+    const char *d = (const char *)src;
+    for (const Part &p : parts) {
+        cudaError_t e = cudaMemcpyAsync(p.dst, d, p.n, cudaMemcpyDeviceToDevice, a->stream);
+        if (e != cudaSuccess) return e;
+        d += p.n;
+    }
+    return cudaSuccess;
+}
+
+// Step parameters whose inputs are a packed state record.
+StepParams adj_params_from_state(const nlbm_adjoint *a, const float *state)
+{
+    StepParams kp = a->sim->kp;
+    const size_t pl = a->plane;
+    kp.fin = state;
+    kp.gin = state + pl * 9 * a->ns;
+    kp.uin = kp.gin + pl * 8;
+    kp.phi_prev = kp.uin + pl * 2;
+    kp.mphi = const_cast<float *>(kp.phi_prev + pl * a->ns);
+    return kp;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlbm_status nlbm_adjoint_workspace_bytes(const nlbm_params *p, int32_t nsteps, int32_t checkpoint_every,
+                                         size_t *bytes)
+{
+    if (!bytes) { set_err(g_err, "bytes is NULL"); return NLBM_EINVAL; }
+    AdjLayout L;
+    nlbm_status st = adj_layout(p, nsteps, checkpoint_every, &L, g_err);
+    if (st != NLBM_OK) return st;
+    *bytes = L.total;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_adjoint_create(const nlbm_params *p, int32_t nsteps, int32_t checkpoint_every, void *dev_workspace,
+                                size_t workspace_bytes, void *cuda_stream, nlbm_adjoint **out)
+{
+    if (!out) { set_err(g_err, "out is NULL"); return NLBM_EINVAL; }
+    *out = nullptr;
+    AdjLayout L;
+    nlbm_status st = adj_layout(p, nsteps, checkpoint_every, &L, g_err);
+    if (st != NLBM_OK) return st;
+    if (!dev_workspace || ((uintptr_t)dev_workspace & 255)) {
+        set_err(g_err, "workspace must be non-NULL and 256-byte aligned");
+        return NLBM_EINVAL;
+    }
+    if (workspace_bytes < L.total) {
+        set_err(g_err, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, L.total);
+        return NLBM_ENOMEM;
+    }
+    nlbm_adjoint *a = new (std::nothrow) nlbm_adjoint();
+    if (!a) { set_err(g_err, "host allocation failed"); return NLBM_ENOMEM; }
+    char *ws = (char *)dev_workspace;
+    st = nlbm_create(p, ws + L.sim, make_layout(p->n_phases - 1, (size_t)p->nx * p->ny, false).total, cuda_stream,
+                     &a->sim);
+    if (st != NLBM_OK) {
+        delete a;
+        return st;
+    }
+    a->ns = p->n_phases - 1;
+    a->N = p->n_phases;
+    a->nsteps = nsteps;
+    a->every = checkpoint_every;
+    a->nckpt = (nsteps + checkpoint_every - 1) / checkpoint_every;
+    a->plane = (size_t)p->nx * p->ny;
+    a->state_floats = adj_state_floats(a->ns, a->plane);
+    a->stream = (cudaStream_t)cuda_stream;
+    a->ws = ws;
+    a->ckpt = (float *)(ws + L.ckpt);
+    a->seg = (float *)(ws + L.seg);
+    const AdjCounts c = adj_counts(a->ns);
+    const size_t pl = a->plane;
+    float *f = (float *)(ws + L.fields);
+    auto take = [&](int planes) {
+        float *q = f;
+        f += (size_t)planes * pl;
+        return q;
+    };
+    const int ns = a->ns;
+    a->T.phi = take(ns);
+    a->T.j = take(2 * ns);
+    a->T.g = take(8);
+    a->T.grad = take(2 * ns);
+    a->T.lap = take(ns);
+    a->T.R = take(2 * ns);
+    a->T.mphi = take(2);
+    a->T.w = take(1);
+    a->T.F = take(2);
+    a->seed[0] = take(c.seedset);
+    a->seed[1] = take(c.seedset);
+    a->A.lF = take(2);
+    a->A.lphi_pw = take(ns);
+    a->A.lj = take(2 * ns);
+    a->A.lgrad = take(2 * ns);
+    a->A.llap = take(ns);
+    a->A.lR = take(2 * ns);
+    a->A.lmphi = take(2);
+    a->A.lg_pull = take(8);
+    a->A.lphi_tot = take(ns);
+    a->A.contrib = take(c.contrib);
+    a->partials = (double *)(ws + L.partials);
+    a->acc = (double *)(ws + L.acc);
+    a->forward_done = false;
+    a->err[0] = 0;
+    *out = a;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_adjoint_forward(nlbm_adjoint *a, const float *dev_phi0, float *dev_phi_final)
+{
+    if (!a || !dev_phi0) return NLBM_EINVAL;
+    nlbm_sim *s = a->sim;
+    s->cur = 0;
+    nlbm_status st = nlbm_set_phi(s, dev_phi0);
+    if (st != NLBM_OK) { memcpy(a->err, s->err, sizeof a->err); return st; }
+    cudaError_t e;
+    for (int k = 0; k < a->nckpt; ++k) {
+        if ((e = adj_save_state(a, a->ckpt + a->state_floats * k)) != cudaSuccess) return adj_fail(a, e, "checkpoint");
+        const int n = (k + 1) * a->every <= a->nsteps ? a->every : a->nsteps - k * a->every;
+        if ((st = nlbm_step(s, n)) != NLBM_OK) { memcpy(a->err, s->err, sizeof a->err); return st; }
+    }
+    if (dev_phi_final && (st = nlbm_get_moments(s, dev_phi_final, nullptr, nullptr)) != NLBM_OK) {
+        memcpy(a->err, s->err, sizeof a->err);
+        return st;
+    }
+    a->forward_done = true;
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_adjoint_backward(nlbm_adjoint *a, const float *dev_seed, float *dev_grad_phi0,
+                                  double *host_grad_sigma, double *host_grad_mobility)
+{
+    if (!a || !dev_seed) return NLBM_EINVAL;
+    if (!a->forward_done) { set_err(a->err, "backward before forward"); return NLBM_EINVAL; }
+    const size_t pl = a->plane, pb = sizeof(float) * pl;
+    const int ns = a->ns, N = a->N, np = N * (N - 1) / 2;
+    const AdjCounts c = adj_counts(ns);
+    cudaError_t e;
+    // the seed of step T: dL/dphi_p(T) for phases 1..N-1 with phase N folded
+    // in (phi_N = 1 - sum), zero for every other output
+    for (int k = 0; k < 2; ++k)
+        if ((e = cudaMemsetAsync(a->seed[k], 0, pb * c.seedset, a->stream)) != cudaSuccess) return adj_fail(a, e, "seed");
+    if ((e = cudaMemsetAsync(a->acc, 0, sizeof(double) * c.contrib, a->stream)) != cudaSuccess) return adj_fail(a, e, "acc");
+    {
+        float *lphi = a->seed[0] + pl * (9 * ns + 8);
+        e = launch_fold_seed(ns, dev_seed, (unsigned)pl, lphi, a->stream);
+        if (e != cudaSuccess) return adj_fail(a, e, "seed fold");
+    }
+    int cur = 0;
+    for (int k = a->nckpt - 1; k >= 0; --k) {
+        const int t0 = k * a->every;
+        const int len = (k + 1) * a->every <= a->nsteps ? a->every : a->nsteps - t0;
+        // rebuild the segment's input states S_t0 .. S_t0+len-1
+        if ((e = adj_load_state(a, a->ckpt + a->state_floats * k)) != cudaSuccess) return adj_fail(a, e, "restore");
+        for (int s = 0; s < len; ++s) {
+            if (s > 0) {
+                nlbm_status st = nlbm_step(a->sim, 1);
+                if (st != NLBM_OK) { memcpy(a->err, a->sim->err, sizeof a->err); return st; }
+            }
+            if ((e = adj_save_state(a, a->seg + a->state_floats * s)) != cudaSuccess) return adj_fail(a, e, "segment");
+        }
+        for (int s = len - 1; s >= 0; --s) {
+            const StepParams kp = adj_params_from_state(a, a->seg + a->state_floats * s);
+            float *so = a->seed[cur], *si = a->seed[cur ^ 1];
+            AdjFields A = a->A;
+            A.lf_out = so;
+            A.lg_out = so + pl * 9 * ns;
+            A.lphi_out = A.lg_out + pl * 8;
+            A.lu_out = A.lphi_out + pl * ns;
+            A.lm_out = A.lu_out + pl * 2;
+            A.lf_in = si;
+            A.lg_in = si + pl * 9 * ns;
+            A.lphi_in = A.lg_in + pl * 8;
+            A.lu_in = A.lphi_in + pl * ns;
+            A.lm_in = A.lu_in + pl * 2;
+            if ((e = launch_reverse_step(ns, kp, a->T, A, a->partials, a->acc, a->stream)) != cudaSuccess)
+                return adj_fail(a, e, "reverse step");
+            a->sim->launches += 9;
+            cur ^= 1;
+        }
+    }
+    // phi0 entered step 1 as its pulled phase populations (f_i = w_i phi0,
+    // so the adjoint is that of phi) and as its phi_prev
+    if (dev_grad_phi0) {
+        const float *lphi_in = a->seed[cur] + pl * (9 * ns + 8);
+        e = launch_add_planes(a->A.lphi_tot, lphi_in, (unsigned)(pl * ns), dev_grad_phi0, a->stream);
+        if (e != cudaSuccess) return adj_fail(a, e, "phi0 gradient");
+    }
+    double acc[kMaxPhases * kMaxPhases + 1];
+    if ((e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * c.contrib, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(a->stream)) != cudaSuccess)
+        return adj_fail(a, e, "gradient download");
+    if (host_grad_sigma) {
+        for (int i = 0; i < N * N; ++i) host_grad_sigma[i] = 0.0;
+        int q = 0;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j, ++q) host_grad_sigma[i * N + j] = host_grad_sigma[j * N + i] = acc[q];
+    }
+    if (host_grad_mobility) *host_grad_mobility = acc[np];
+    return NLBM_OK;
+}
+
+nlbm_status nlbm_adjoint_reverse_step(nlbm_adjoint *a, const float *dev_state, const float *dev_seed_out,
+                                      float *dev_seed_in, double *host_grad_sigma, double *host_grad_mobility)
+{
+    if (!a || !dev_state || !dev_seed_out || !dev_seed_in) return NLBM_EINVAL;
+    const size_t pl = a->plane, pb = sizeof(float) * pl;
+    const int ns = a->ns, N = a->N, np = N * (N - 1) / 2;
+    const AdjCounts c = adj_counts(ns);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(a->seed[0], dev_seed_out, pb * c.seedset, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(a->acc, 0, sizeof(double) * c.contrib, a->stream)) != cudaSuccess)
+        return adj_fail(a, e, "seed");
+    AdjFields A = a->A;
+    float *so = a->seed[0], *si = a->seed[1];
+    A.lf_out = so;
+    A.lg_out = so + pl * 9 * ns;
+    A.lphi_out = A.lg_out + pl * 8;
+    A.lu_out = A.lphi_out + pl * ns;
+    A.lm_out = A.lu_out + pl * 2;
+    A.lf_in = si;
+    A.lg_in = si + pl * 9 * ns;
+    A.lphi_in = A.lg_in + pl * 8;
+    A.lu_in = A.lphi_in + pl * ns;
+    A.lm_in = A.lu_in + pl * 2;
+    const StepParams kp = adj_params_from_state(a, dev_state);
+    if ((e = launch_reverse_step(ns, kp, a->T, A, a->partials, a->acc, a->stream)) != cudaSuccess)
+        return adj_fail(a, e, "reverse step");
+    a->sim->launches += 9;
+    double acc[kMaxPhases * kMaxPhases + 1];
+    if ((e = cudaMemcpyAsync(dev_seed_in, si, pb * c.seedset, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * c.contrib, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(a->stream)) != cudaSuccess)
+        return adj_fail(a, e, "reverse step results");
+    if (host_grad_sigma) {
+        for (int i = 0; i < N * N; ++i) host_grad_sigma[i] = 0.0;
+        int q = 0;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j, ++q) host_grad_sigma[i * N + j] = host_grad_sigma[j * N + i] = acc[q];
+    }
+    if (host_grad_mobility) *host_grad_mobility = acc[np];
+    return NLBM_OK;
+}
+
+int64_t nlbm_adjoint_kernel_launches(const nlbm_adjoint *a) { return a ? a->sim->launches : -1; }
+
+void nlbm_adjoint_destroy(nlbm_adjoint *a)
+{
+    if (!a) return;
+    nlbm_destroy(a->sim);
+    delete a;
+}
+
+const char *nlbm_adjoint_last_error(const nlbm_adjoint *a) { return a ? a->err : g_err; }
 
 }  // extern "C"
 

@@ -42,6 +42,9 @@ struct StepParams {
     float beta2[kMaxPhases][kMaxPhases];  // 2 beta_pq = 6 sigma_pq / eps (Eq. (15))
     float kap[kMaxPhases][kMaxPhases];    // -k_pq = 3 eps sigma_pq / 4 (Eq. (15))
     float four_over_eps;       // 4 / eps
+    float unit_delta2;         // delta^2 of the smooth unit vector (0: thresholded reading)
+    float six_over_eps;        // d beta2 / d sigma (adjoint)
+    float three_eps_over_4;    // d kap / d sigma (adjoint)
     float mob;                 // M
     float s1;                  // 1 / tau_f, tau_f = 0.5 + 3 M (Eq. (20))
     float model_n;             // Model A exponent n

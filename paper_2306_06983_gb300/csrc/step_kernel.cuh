@@ -167,10 +167,12 @@ __device__ __forceinline__ void exact_pair(float c, float h, float &plus, float 
     minus = h >= 0.f ? small : big;
 }
 
-// Unit vector with the zero-gradient reading: 0 when |v|^2 <= 1e-24.
-__device__ __forceinline__ float inv_norm(float vx, float vy)
+// 1/|v| of a unit vector: with the zero-gradient reading 0 when |v|^2 <=
+// 1e-24, or the smooth reading 1/sqrt(|v|^2 + delta^2) when delta2 > 0.
+__device__ __forceinline__ float inv_norm(float vx, float vy, float delta2)
 {
     const float n2 = vx * vx + vy * vy;
+    if (delta2 > 0.f) return rsqrtf(n2 + delta2);
     return n2 > 1e-24f ? rsqrtf(n2) : 0.0f;
 }
 
@@ -333,7 +335,7 @@ __device__ __forceinline__ void source_terms(const StepParams &P, const float (&
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             a[q] = P.four_over_eps * ph[q] * (1.f - ph[q]);
-            const float r = inv_norm(gx[q], gy[q]);
+            const float r = inv_norm(gx[q], gy[q], P.unit_delta2);
             nxv[q] = gx[q] * r;
             nyv[q] = gy[q] * r;
             const float pc = fmaxf(ph[q], 0.f);
@@ -371,7 +373,7 @@ __device__ __forceinline__ void source_terms(const StepParams &P, const float (&
             for (int q = p + 1; q < N; ++q) {
                 const float vx = ph[q] * gx[p] - ph[p] * gx[q];
                 const float vy = ph[q] * gy[p] - ph[p] * gy[q];
-                const float c = P.four_over_eps * ph[p] * ph[q] * inv_norm(vx, vy);
+                const float c = P.four_over_eps * ph[p] * ph[q] * inv_norm(vx, vy, P.unit_delta2);
                 if (p < NS) { Rx[p] += c * vx; Ry[p] += c * vy; }
                 if (q < NS) { Rx[q] -= c * vx; Ry[q] -= c * vy; }
             }

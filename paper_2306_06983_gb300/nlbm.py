@@ -48,6 +48,7 @@ class nlbm_params(ctypes.Structure):
         ("sigma", ctypes.POINTER(ctypes.c_double)),
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("unit_delta", ctypes.c_double),
     ]
 
 
@@ -95,6 +96,16 @@ def load_library(path: str = LIB_PATH):
         "nlbm_batch_kernel_launches": (ctypes.c_int64, [vp]),
         "nlbm_batch_destroy": (None, [vp]),
         "nlbm_batch_last_error": (ctypes.c_char_p, [vp]),
+        "nlbm_adjoint_workspace_bytes": (st, [P(nlbm_params), ctypes.c_int32, ctypes.c_int32,
+                                              P(ctypes.c_size_t)]),
+        "nlbm_adjoint_create": (st, [P(nlbm_params), ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, vp,
+                                     P(vp)]),
+        "nlbm_adjoint_forward": (st, [vp, vp, vp]),
+        "nlbm_adjoint_backward": (st, [vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]),
+        "nlbm_adjoint_kernel_launches": (ctypes.c_int64, [vp]),
+        "nlbm_adjoint_reverse_step": (st, [vp, vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]),
+        "nlbm_adjoint_destroy": (None, [vp]),
+        "nlbm_adjoint_last_error": (ctypes.c_char_p, [vp]),
         "nlbm_kernel_launches": (ctypes.c_int64, [vp]),
         "nlbm_set_tile": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
         "nlbm_get_tile": (st, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
@@ -146,6 +157,7 @@ def make_params(p: dict):
     st = p.get("storage", NLBM_STORE_F32)
     s.storage = STORAGE_CODES[st] if isinstance(st, str) else int(st)
     s.reserved = 0
+    s.unit_delta = float(p.get("unit_delta", 0.0))
     return s, (rho, mu, sigma)
 
 
@@ -528,3 +540,169 @@ class Batch:
     @property
     def kernel_launches(self) -> int:
         return nlbm_batch_kernel_launches(self.h)
+
+
+# ------------------------------------------------------------ adjoint
+
+def _check_adj(st: int, handle=None):
+    if st != NLBM_OK:
+        msg = load_library().nlbm_adjoint_last_error(handle).decode()
+        raise NlbmError(st, msg)
+
+
+def nlbm_adjoint_workspace_bytes(params: dict, nsteps: int, every: int) -> int:
+    s, keep = make_params(params)
+    out = ctypes.c_size_t(0)
+    _check_adj(load_library().nlbm_adjoint_workspace_bytes(ctypes.byref(s), nsteps, every, ctypes.byref(out)))
+    return int(out.value)
+
+
+def nlbm_adjoint_create(params: dict, nsteps: int, every: int, workspace_ptr: int, workspace_bytes: int,
+                        stream_ptr: int) -> int:
+    s, keep = make_params(params)
+    h = ctypes.c_void_p()
+    _check_adj(load_library().nlbm_adjoint_create(ctypes.byref(s), nsteps, every, ctypes.c_void_p(workspace_ptr),
+                                                  workspace_bytes, ctypes.c_void_p(stream_ptr), ctypes.byref(h)))
+    return h.value
+
+
+def nlbm_adjoint_forward(h, phi0_ptr: int, phi_final_ptr):
+    _check_adj(load_library().nlbm_adjoint_forward(h, ctypes.c_void_p(phi0_ptr), phi_final_ptr), h)
+
+
+def nlbm_adjoint_backward(h, seed_ptr: int, grad_phi0_ptr, N: int):
+    gs = (ctypes.c_double * (N * N))()
+    gm = ctypes.c_double(0.0)
+    _check_adj(load_library().nlbm_adjoint_backward(h, ctypes.c_void_p(seed_ptr), grad_phi0_ptr, gs,
+                                                    ctypes.byref(gm)), h)
+    return np.array(gs[:], dtype=np.float64).reshape(N, N), float(gm.value)
+
+
+def nlbm_adjoint_kernel_launches(h) -> int:
+    return int(load_library().nlbm_adjoint_kernel_launches(h))
+
+
+def nlbm_adjoint_destroy(h):
+    load_library().nlbm_adjoint_destroy(h)
+
+
+def nlbm_adjoint_last_error(h=None) -> str:
+    return load_library().nlbm_adjoint_last_error(h).decode()
+
+
+class AdjointRun:
+    """One differentiable run: nsteps forward steps with a checkpoint every
+    `every` steps, then the reverse sweep for a seed dL/dphi(T)."""
+
+    def __init__(self, params: dict, nsteps: int, every: int = 50, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.params = dict(params)
+        self.N, self.nx, self.ny = int(params["n_phases"]), int(params["nx"]), int(params["ny"])
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = nlbm_adjoint_workspace_bytes(params, nsteps, every)
+        self.workspace = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.h = ctypes.c_void_p(nlbm_adjoint_create(params, nsteps, every, aligned, n, self.stream.cuda_stream))
+
+    def forward(self, phi0):
+        """phi0 [N-1, ny, nx] -> phi(T) [N, ny, nx] (CUDA tensor)."""
+        torch = self.torch
+        t = torch.as_tensor(phi0).to(device=self.device, dtype=torch.float32).contiguous()
+        self._phi0 = t
+        out = torch.empty((self.N, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        nlbm_adjoint_forward(self.h, t.data_ptr(), ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def backward(self, seed):
+        """seed = dL/dphi(T) [N, ny, nx] -> (dL/dphi0 [N-1, ny, nx],
+        dL/dsigma [N, N] (symmetric; entry (p, q) is the derivative with
+        respect to the pair's single value), dL/dmobility)."""
+        torch = self.torch
+        sd = torch.as_tensor(seed).to(device=self.device, dtype=torch.float32).contiguous()
+        g0 = torch.empty((self.N - 1, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        gs, gm = nlbm_adjoint_backward(self.h, sd.data_ptr(), ctypes.c_void_p(g0.data_ptr()), self.N)
+        return g0, gs, gm
+
+    def reverse_step(self, state, seed_out):
+        """One reverse step from a packed state record [f 9(N-1), g 8, u 2,
+        phi N-1, m_phi 2 planes] and the adjoint seed of its outputs [f
+        9(N-1), g 8, phi N-1, u 2, m_phi 2 planes]; returns the adjoint of
+        its inputs in the seed layout and the parameter gradients."""
+        torch = self.torch
+        st = torch.as_tensor(state).to(device=self.device, dtype=torch.float32).contiguous()
+        sd = torch.as_tensor(seed_out).to(device=self.device, dtype=torch.float32).contiguous()
+        out = torch.empty_like(sd)
+        gs = (ctypes.c_double * (self.N * self.N))()
+        gm = ctypes.c_double(0.0)
+        _check_adj(load_library().nlbm_adjoint_reverse_step(self.h, ctypes.c_void_p(st.data_ptr()),
+                                                            ctypes.c_void_p(sd.data_ptr()),
+                                                            ctypes.c_void_p(out.data_ptr()), gs,
+                                                            ctypes.byref(gm)), self.h)
+        return out, np.array(gs[:]).reshape(self.N, self.N), float(gm.value)
+
+    @property
+    def kernel_launches(self) -> int:
+        return nlbm_adjoint_kernel_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            nlbm_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pair_list(N: int):
+    return [(p, q) for p in range(N) for q in range(p + 1, N)]
+
+
+def _make_function():
+    import torch
+
+    class NPhaseLBM(torch.autograd.Function):
+        """phi(T) = step^T(phi0; sigma, mobility) through the CUDA library;
+        backward is the library's adjoint (checkpoint every `every` steps).
+        sigma_pairs: tensor of the N(N-1)/2 pairwise tensions in the order
+        (1,2), (1,3), ..., (N-1,N); mobility: 0-d tensor."""
+
+        @staticmethod
+        def forward(ctx, phi0, sigma_pairs, mobility, params, nsteps, every):
+            N = int(params["n_phases"])
+            sig = np.zeros((N, N))
+            for (p, q), v in zip(pair_list(N), sigma_pairs.detach().cpu().double().tolist()):
+                sig[p, q] = sig[q, p] = v
+            q = dict(params, sigma=sig.tolist(), mobility=float(mobility.detach().cpu()))
+            run = AdjointRun(q, nsteps, every, device=phi0.device)
+            out = run.forward(phi0.detach())
+            ctx.run = run
+            ctx.N = N
+            ctx.sdtype = sigma_pairs.dtype
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g0, gs, gm = ctx.run.backward(grad_out.contiguous())
+            N = ctx.N
+            gpairs = torch.tensor([gs[p, q] for p, q in pair_list(N)], dtype=ctx.sdtype)
+            ctx.run.close()
+            return g0, gpairs, torch.tensor(gm, dtype=ctx.sdtype), None, None, None
+
+    return NPhaseLBM
+
+
+_FN = None
+
+
+def nphase_lbm(phi0, sigma_pairs, mobility, params: dict, nsteps: int, every: int = 50):
+    """Differentiable N-phase LBM run (autograd through the CUDA adjoint)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    return _FN.apply(phi0, sigma_pairs, mobility, params, nsteps, every)

@@ -242,3 +242,18 @@ def lens_ensemble(count=64, seed=SEED, sizes=LENS_SIZES):
             model, n = "A", MODEL_A_SWEEP[(k - half) * len(MODEL_A_SWEEP) // max(count - half, 1)]
         out.append(lens(nx, ny, 0.2 * ny, 0.01, s13, s23, model=model, model_a_n=n))
     return out
+
+
+def adjoint_problem(nx=256, ny=256, seed=SEED, sigma=(0.01, 0.01, 0.01), unit_delta=1e-3):
+    """Three-phase, Model B, periodic problem of the gradient studies: disks
+    of phases 2 and 3 (seeded positions, radii U[nx/16, nx/8] but at least
+    1.5 eps) in phase 1; densities 1, relaxation time 1, mobility 0.1,
+    eps = 4; sigma = (sigma_12, sigma_13, sigma_23); unit vectors in the
+    smooth reading with delta = unit_delta (differentiable)."""
+    rmin, rmax = max(6.0, nx / 16.0), max(7.0, nx / 8.0)
+    n_disks = max(2, int(round(8 * nx * ny / 256 ** 2)))
+    p, phi0 = random_disks(nx, ny, 3, n_disks, rmin, rmax, seed=seed, model="B")
+    s12, s13, s23 = sigma
+    p = base_params(nx, ny, 3, model="B", sigma=[[0.0, s12, s13], [s12, 0.0, s23], [s13, s23, 0.0]])
+    p["unit_delta"] = float(unit_delta)
+    return p, phi0

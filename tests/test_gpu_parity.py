@@ -153,6 +153,37 @@ def test_droplets64_2000_steps(model, n):
     assert np.abs(gu - ou).max() <= max(1e-8, 3 * spread[1])
 
 
+@pytest.mark.parametrize("case", ["droplets64_B", "droplets64_A1", "droplets64_A2"])
+def test_smooth_reading_meets_2000_step_target(case):
+    """With the sources' unit vectors in the smooth reading (delta = 1e-3,
+    both here and in the oracle) the FP32 path follows the FP64 oracle to
+    max |d phi| <= 1e-5 after 2000 steps, with per-phase mass drift <= 1e-6:
+    the method is then well conditioned, and the rounding amplification of
+    the thresholded reading (see test_droplets64_2000_steps) is gone."""
+    p, phi0 = CASES[case]()
+    p = dict(p, unit_delta=1e-3)
+    phi0 = f32(phi0)
+    m0, g = gpu_run(p, phi0, 2000)
+    gphi, gu, gP, m1 = g[0]
+    (ophi, ou, oP), = oracle_run(p, phi0, 2000)
+    d = np.abs(gphi - ophi)
+    print(f"\n{case} delta=1e-3: max|dphi| {d.max():.2e} mean {d.mean():.2e} max|du| "
+          f"{np.abs(gu - ou).max():.2e} drift {(np.abs(m1 - m0) / m0).max():.2e}")
+    assert d.max() <= 1e-5
+    assert np.all(np.abs(m1 - m0) / m0 <= 1e-6)
+    assert np.abs(gu - ou).max() <= 1e-7
+
+
+def test_smooth_reading_disks256_500_steps():
+    p, phi0 = W.disks_256("B")
+    p = dict(p, unit_delta=1e-3)
+    phi0 = f32(phi0)
+    m0, g = gpu_run(p, phi0, 500)
+    (ophi, ou, oP), = oracle_run(p, phi0, 500)
+    assert np.abs(g[0][0] - ophi).max() <= 1e-5
+    assert np.all(np.abs(g[0][3] - m0) / m0 <= 1e-6)
+
+
 def test_flat_band_2000_steps():
     """A flat interface over 2000 steps: within 3x the FP32 spread."""
     nx, ny = 16, 64

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from paper_2306_06983_gb300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
@@ -265,3 +266,32 @@ def test_lens_closed_form_reproduces_table3():
     # symmetric tensions: 60 degree caps, equal heights
     hd, ha, hb, ta, tb = lens_equilibrium(1.0, 1.0, 1.0, 3.0)
     assert abs(ta - np.pi / 3) < 1e-12 and abs(ha - hb) < 1e-12
+
+
+def test_smooth_unit_vector_reading(oracle_built):
+    """The smooth reading v / sqrt(|v|^2 + delta^2) of the sources' unit
+    vectors: a zero gradient still gives R = 0, at interface gradients
+    (|grad phi| ~ 1/eps) the source differs from the thresholded reading by
+    O(delta^2 / |v|^2), and the two-phase reduction of Model B (R = 4 phi (1 -
+    phi) / eps n) holds with the smoothed n."""
+    from oracle.oracle import point_source
+    for model in ("A", "B"):
+        p = W.base_params(1, 1, 3, model=model, model_a_n=1.0)
+        ph = np.array([0.3, 0.5, 0.2])
+        g = np.array([[0.05, -0.02], [-0.08, 0.01], [0.03, 0.01]])
+        r0 = point_source(p, ph, g)
+        r1 = point_source(dict(p, unit_delta=1e-3), ph, g)
+        r2 = point_source(dict(p, unit_delta=2e-3), ph, g)
+        # |v| ~ 0.02 here: the smooth reading moves R by O(delta^2 / |v|^2)
+        assert np.abs(r1 - r0).max() < 1e-2 * np.abs(r0).max()
+        ratio = np.abs(r2 - r0).max() / np.abs(r1 - r0).max()
+        assert 3.6 < ratio < 4.1, ratio   # 4 (delta^2) less the next order
+        z = point_source(dict(p, unit_delta=1e-3), ph, np.zeros((3, 2)))
+        assert np.all(z == 0.0)
+    p = W.base_params(1, 1, 2, model="B")
+    phi, gv = 0.3, np.array([0.04, -0.03])
+    d = 1e-3
+    R = point_source(dict(p, unit_delta=d), np.array([phi, 1 - phi]), np.array([gv, -gv]))
+    # v = phi_2 grad phi_1 - phi_1 grad phi_2 = grad phi_1 (phi_1 + phi_2 = 1)
+    n = gv / np.sqrt(gv @ gv + d * d)
+    np.testing.assert_allclose(R[0], 4 * phi * (1 - phi) / 4.0 * n, rtol=1e-12, atol=1e-15)
