@@ -494,9 +494,9 @@ __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
         A.lm_in[k] = a_mpx;
         A.lm_in[pl + k] = a_mpy;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) A.contrib[(size_t)q * pl + k] = dsig[q];
+        for (int q = 0; q < NP; ++q) A.gacc[(size_t)q * pl + k] += (double)dsig[q];
         // s1 = 1 / (1/2 + 3 M): d s1 / dM = -3 s1^2
-        A.contrib[(size_t)NP * pl + k] = -3.f * s1 * s1 * a_s1;
+        A.gacc[(size_t)NP * pl + k] += (double)(-3.f * s1 * s1 * a_s1);
     }
 }
 
@@ -582,7 +582,7 @@ __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
             A.lgrad[(size_t)(2 * p) * pl + k] = a_gx[p] - a_gx[NS];
             A.lgrad[(size_t)(2 * p + 1) * pl + k] = a_gy[p] - a_gy[NS];
         }
-        A.contrib[(size_t)NP * pl + k] += dM;
+        A.gacc[(size_t)NP * pl + k] += (double)dM;
     }
 }
 
@@ -635,14 +635,14 @@ __global__ void rev_pull_kernel(const StepParams P, AdjFields A)
 constexpr int kRedThreads = 256;
 
 // Fixed-order FP64 sums of K per-node fields, added to acc[K].
-__global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const float *__restrict__ contrib, int K,
+__global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const double *__restrict__ contrib, int K,
                                                                      unsigned n, double *partials)
 {
     __shared__ double red[kRedThreads];
     for (int c = 0; c < K; ++c) {
         double v = 0.0;
         for (unsigned k = blockIdx.x * kRedThreads + threadIdx.x; k < n; k += gridDim.x * kRedThreads)
-            v += (double)contrib[(size_t)c * n + k];
+            v += contrib[(size_t)c * n + k];
         red[threadIdx.x] = v;
         __syncthreads();
         for (int s = kRedThreads / 2; s > 0; s >>= 1) {
@@ -660,7 +660,7 @@ __global__ void reduce_final_kernel(const double *__restrict__ partials, int K, 
     if (c >= K) return;
     double v = 0.0;
     for (int b = 0; b < nblocks; ++b) v += partials[(size_t)b * K + c];
-    acc[c] += v;
+    acc[c] = v;
 }
 
 int blocks_for(unsigned n)
@@ -671,10 +671,8 @@ int blocks_for(unsigned n)
 }
 
 template <int NS>
-cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, double *partials,
-                            double *acc, cudaStream_t st)
+cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st)
 {
-    constexpr int NP = (NS + 1) * NS / 2;
     const int nb = blocks_for(P.plane);
     tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
     tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
@@ -683,8 +681,6 @@ cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFiel
     rev_source_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
     rev_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, A);
     rev_pull_kernel<NS><<<nb, 256, 0, st>>>(P, A);
-    reduce_partial_kernel<<<kAdjRedBlocks, kRedThreads, 0, st>>>(A.contrib, NP + 1, P.plane, partials);
-    reduce_final_kernel<<<1, 64, 0, st>>>(partials, NP + 1, kAdjRedBlocks, acc);
     return cudaGetLastError();
 }
 
@@ -704,16 +700,23 @@ __global__ void add_planes_kernel(const float *__restrict__ a, const float *__re
 
 }  // namespace
 
-cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A,
-                                double *partials, double *acc, cudaStream_t st)
+cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st)
 {
     switch (ns) {
 #define NLBM_CASE(K) \
-    case K: return reverse_step_ns<K>(P, T, A, partials, acc, st);
+    case K: return reverse_step_ns<K>(P, T, A, st);
         NLBM_CASE(1) NLBM_CASE(2) NLBM_CASE(3) NLBM_CASE(4) NLBM_CASE(5) NLBM_CASE(6) NLBM_CASE(7)
 #undef NLBM_CASE
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_grad_reduce(const double *gacc, int K, unsigned plane, double *partials, double *acc,
+                               cudaStream_t st)
+{
+    reduce_partial_kernel<<<kAdjRedBlocks, kRedThreads, 0, st>>>(gacc, K, plane, partials);
+    reduce_final_kernel<<<1, 64, 0, st>>>(partials, K, kAdjRedBlocks, acc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fold_seed(int ns, const float *seed, unsigned plane, float *lphi, cudaStream_t st)

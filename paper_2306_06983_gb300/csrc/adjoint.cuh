@@ -40,13 +40,17 @@ struct AdjFields {
     float *lmphi;    // [2]
     float *lg_pull;  // [8]
     float *lphi_tot; // [N-1]
-    float *contrib;  // [N(N-1)/2 + 1] per-node dL/dsigma_pq (pair order p<q) and dL/dM
+    double *gacc;    // [N(N-1)/2 + 1] per-node sums over the steps of dL/dsigma_pq
+                     // (pair order p<q) and dL/dM, FP64
 };
 
 // Tape and reverse of one step whose input state P describes (P.fin, P.gin,
-// P.phi_prev, P.uin, P.mphi); adds this step's parameter gradients to acc.
-cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A,
-                                double *partials, double *acc, cudaStream_t st);
+// P.phi_prev, P.uin, P.mphi); adds this step's parameter-gradient terms to
+// A.gacc node by node.
+cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st);
+// acc[c] = sum over nodes of gacc[c][node], c < K, in a fixed order (FP64).
+cudaError_t launch_grad_reduce(const double *gacc, int K, unsigned plane, double *partials, double *acc,
+                               cudaStream_t st);
 // lphi[p] = seed[p] - seed[N-1] for the N-1 solved phases.
 cudaError_t launch_fold_seed(int ns, const float *seed, unsigned plane, float *lphi, cudaStream_t st);
 // out = a + b over n floats.

@@ -945,6 +945,11 @@ struct nlbm_adjoint {
     float *seed[2];            // two sets of step-output adjoints
     AdjFields A;               // intermediates (the seed pointers are set per step)
     double *partials, *acc;    // [kAdjRedBlocks][NP+1], [NP+1]
+    float *seed_buf;           // [N][plane] copy of the caller's dL/dphi(T)
+    float *grad_buf;           // [N-1][plane] dL/dphi_0
+    int final_set;             // seed set holding step 1's input adjoints
+    cudaGraphExec_t graph;     // the whole reverse sweep, captured on first use
+    bool graph_tried;
     bool forward_done;
     char err[512];
 };
@@ -964,7 +969,8 @@ struct AdjCounts {
 AdjCounts adj_counts(int ns)
 {
     const int np = (ns + 1) * ns / 2;
-    return AdjCounts{8 * ns + 13, 10 * ns + 12, 9 * ns + 12, np + 1};
+    // tape, one seed set, intermediates, per-node gradient sums (FP64: 2 floats each)
+    return AdjCounts{8 * ns + 13, 10 * ns + 12, 9 * ns + 12, 2 * (np + 1)};
 }
 
 struct AdjLayout {
@@ -994,7 +1000,8 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
     L->sim = take(make_layout(ns, plane, false).total);
     L->ckpt = take(sizeof(float) * adj_state_floats(ns, plane) * nckpt);
     L->seg = take(sizeof(float) * adj_state_floats(ns, plane) * (size_t)(every < nsteps ? every : nsteps));
-    L->fields = take(sizeof(float) * plane * (size_t)(c.tape + 2 * c.seedset + c.inter + c.contrib));
+    // the FP64 per-node sums come first (8-byte alignment)
+    L->fields = take(sizeof(float) * plane * (size_t)(c.contrib + c.tape + 2 * c.seedset + c.inter + 2 * ns + 1));
     L->partials = take(sizeof(double) * kAdjRedBlocks * c.contrib);
     L->acc = take(sizeof(double) * c.contrib);
     L->total = off;
@@ -1051,6 +1058,87 @@ StepParams adj_params_from_state(const nlbm_adjoint *a, const float *state)
     kp.phi_prev = kp.uin + pl * 2;
     kp.mphi = const_cast<float *>(kp.phi_prev + pl * a->ns);
     return kp;
+}
+
+// Adjoint-field pointers for a step whose output adjoints are seed set so
+// and input adjoints seed set si.
+AdjFields adj_fields(const nlbm_adjoint *a, float *so, float *si)
+{
+    const size_t pl = a->plane;
+    const int ns = a->ns;
+    AdjFields A = a->A;
+    A.lf_out = so;
+    A.lg_out = so + pl * 9 * ns;
+    A.lphi_out = A.lg_out + pl * 8;
+    A.lu_out = A.lphi_out + pl * ns;
+    A.lm_out = A.lu_out + pl * 2;
+    A.lf_in = si;
+    A.lg_in = si + pl * 9 * ns;
+    A.lphi_in = A.lg_in + pl * 8;
+    A.lu_in = A.lphi_in + pl * ns;
+    A.lm_in = A.lu_in + pl * 2;
+    return A;
+}
+
+// Kernel launches of one reverse sweep (counted, not queried).
+int64_t adj_sweep_launches(const nlbm_adjoint *a)
+{
+    // fold + per step: 7 reverse kernels; recompute: one step kernel per
+    // rebuilt state; the phi0 sum and the two-kernel reduction
+    return 1 + 7 * (int64_t)a->nsteps + (a->nsteps - a->nckpt) + 1 + 2;
+}
+
+// The reverse sweep, asynchronous and capturable: seeds from seed_buf,
+// dL/dphi_0 into grad_buf, dL/dsigma and dL/dM into acc.
+cudaError_t adj_backward_body(nlbm_adjoint *a)
+{
+    const size_t pl = a->plane, pb = sizeof(float) * pl;
+    const int ns = a->ns;
+    const AdjCounts c = adj_counts(ns);
+    cudaError_t e;
+    for (int k = 0; k < 2; ++k)
+        if ((e = cudaMemsetAsync(a->seed[k], 0, pb * c.seedset, a->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a->A.gacc, 0, pb * c.contrib, a->stream)) != cudaSuccess) return e;
+    if ((e = launch_fold_seed(ns, a->seed_buf, (unsigned)pl, a->seed[0] + pl * (9 * ns + 8), a->stream)) != cudaSuccess)
+        return e;
+    int cur = 0;
+    for (int k = a->nckpt - 1; k >= 0; --k) {
+        const int t0 = k * a->every;
+        const int len = (k + 1) * a->every <= a->nsteps ? a->every : a->nsteps - t0;
+        // rebuild the segment's input states S_t0 .. S_t0+len-1 in place
+        if ((e = cudaMemcpyAsync(a->seg, a->ckpt + a->state_floats * k, sizeof(float) * a->state_floats,
+                                 cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess)
+            return e;
+        for (int s = 1; s < len; ++s) {
+            const float *in = a->seg + a->state_floats * (s - 1);
+            float *out = a->seg + a->state_floats * s;
+            StepParams kp = adj_params_from_state(a, in);
+            kp.fout = out;
+            kp.gout = out + pl * 9 * ns;
+            kp.uout = kp.gout + pl * 8;
+            kp.phi = kp.uout + pl * 2;
+            kp.mphi = kp.phi + pl * ns;   // m_phi is updated in place: copy it over first
+            kp.pout = nullptr;
+            if ((e = cudaMemcpyAsync(kp.mphi, in + (kp.mphi - out), pb * 2, cudaMemcpyDeviceToDevice, a->stream)) !=
+                cudaSuccess)
+                return e;
+            if ((e = launch_step(a->sim, kp)) != cudaSuccess) return e;
+        }
+        for (int s = len - 1; s >= 0; --s) {
+            const StepParams kp = adj_params_from_state(a, a->seg + a->state_floats * s);
+            const AdjFields A = adj_fields(a, a->seed[cur], a->seed[cur ^ 1]);
+            if ((e = launch_reverse_step(ns, kp, a->T, A, a->stream)) != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
+    a->final_set = cur;
+    // phi0 entered step 1 as its pulled phase populations (f_i = w_i phi0,
+    // so the adjoint is that of phi) and as its phi_prev
+    const float *lphi_in = a->seed[cur] + pl * (9 * ns + 8);
+    if ((e = launch_add_planes(a->A.lphi_tot, lphi_in, (unsigned)(pl * ns), a->grad_buf, a->stream)) != cudaSuccess)
+        return e;
+    const int np = (ns + 1) * ns / 2;
+    return launch_grad_reduce(a->A.gacc, np + 1, (unsigned)pl, a->partials, a->acc, a->stream);
 }
 
 }  // namespace
@@ -1113,6 +1201,7 @@ nlbm_status nlbm_adjoint_create(const nlbm_params *p, int32_t nsteps, int32_t ch
         return q;
     };
     const int ns = a->ns;
+    a->A.gacc = (double *)take(c.contrib);
     a->T.phi = take(ns);
     a->T.j = take(2 * ns);
     a->T.g = take(8);
@@ -1133,9 +1222,13 @@ nlbm_status nlbm_adjoint_create(const nlbm_params *p, int32_t nsteps, int32_t ch
     a->A.lmphi = take(2);
     a->A.lg_pull = take(8);
     a->A.lphi_tot = take(ns);
-    a->A.contrib = take(c.contrib);
+    a->seed_buf = take(ns + 1);
+    a->grad_buf = take(ns);
     a->partials = (double *)(ws + L.partials);
     a->acc = (double *)(ws + L.acc);
+    a->final_set = 0;
+    a->graph = nullptr;
+    a->graph_tried = false;
     a->forward_done = false;
     a->err[0] = 0;
     *out = a;
@@ -1171,61 +1264,38 @@ nlbm_status nlbm_adjoint_backward(nlbm_adjoint *a, const float *dev_seed, float 
     const size_t pl = a->plane, pb = sizeof(float) * pl;
     const int ns = a->ns, N = a->N, np = N * (N - 1) / 2;
     const AdjCounts c = adj_counts(ns);
-    cudaError_t e;
-    // the seed of step T: dL/dphi_p(T) for phases 1..N-1 with phase N folded
-    // in (phi_N = 1 - sum), zero for every other output
-    for (int k = 0; k < 2; ++k)
-        if ((e = cudaMemsetAsync(a->seed[k], 0, pb * c.seedset, a->stream)) != cudaSuccess) return adj_fail(a, e, "seed");
-    if ((e = cudaMemsetAsync(a->acc, 0, sizeof(double) * c.contrib, a->stream)) != cudaSuccess) return adj_fail(a, e, "acc");
-    {
-        float *lphi = a->seed[0] + pl * (9 * ns + 8);
-        e = launch_fold_seed(ns, dev_seed, (unsigned)pl, lphi, a->stream);
-        if (e != cudaSuccess) return adj_fail(a, e, "seed fold");
-    }
-    int cur = 0;
-    for (int k = a->nckpt - 1; k >= 0; --k) {
-        const int t0 = k * a->every;
-        const int len = (k + 1) * a->every <= a->nsteps ? a->every : a->nsteps - t0;
-        // rebuild the segment's input states S_t0 .. S_t0+len-1
-        if ((e = adj_load_state(a, a->ckpt + a->state_floats * k)) != cudaSuccess) return adj_fail(a, e, "restore");
-        for (int s = 0; s < len; ++s) {
-            if (s > 0) {
-                nlbm_status st = nlbm_step(a->sim, 1);
-                if (st != NLBM_OK) { memcpy(a->err, a->sim->err, sizeof a->err); return st; }
-            }
-            if ((e = adj_save_state(a, a->seg + a->state_floats * s)) != cudaSuccess) return adj_fail(a, e, "segment");
+    cudaError_t e = cudaMemcpyAsync(a->seed_buf, dev_seed, pb * N, cudaMemcpyDeviceToDevice, a->stream);
+    if (e != cudaSuccess) return adj_fail(a, e, "seed copy");
+    // The sweep is the same sequence of launches for every call of this
+    // handle: capture it into a CUDA graph once (on a capturable stream) and
+    // replay it.
+    if (!a->graph && !a->graph_tried && a->stream != nullptr) {
+        a->graph_tried = true;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(a->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaError_t eb = adj_backward_body(a);
+            cudaError_t ec = cudaStreamEndCapture(a->stream, &g);
+            if (eb == cudaSuccess && ec == cudaSuccess && cudaGraphInstantiate(&a->graph, g, 0) != cudaSuccess)
+                a->graph = nullptr;
+            if (g) cudaGraphDestroy(g);
         }
-        for (int s = len - 1; s >= 0; --s) {
-            const StepParams kp = adj_params_from_state(a, a->seg + a->state_floats * s);
-            float *so = a->seed[cur], *si = a->seed[cur ^ 1];
-            AdjFields A = a->A;
-            A.lf_out = so;
-            A.lg_out = so + pl * 9 * ns;
-            A.lphi_out = A.lg_out + pl * 8;
-            A.lu_out = A.lphi_out + pl * ns;
-            A.lm_out = A.lu_out + pl * 2;
-            A.lf_in = si;
-            A.lg_in = si + pl * 9 * ns;
-            A.lphi_in = A.lg_in + pl * 8;
-            A.lu_in = A.lphi_in + pl * ns;
-            A.lm_in = A.lu_in + pl * 2;
-            if ((e = launch_reverse_step(ns, kp, a->T, A, a->partials, a->acc, a->stream)) != cudaSuccess)
-                return adj_fail(a, e, "reverse step");
-            a->sim->launches += 9;
-            cur ^= 1;
-        }
+        cudaGetLastError();   // a failed capture leaves the direct path
     }
-    // phi0 entered step 1 as its pulled phase populations (f_i = w_i phi0,
-    // so the adjoint is that of phi) and as its phi_prev
-    if (dev_grad_phi0) {
-        const float *lphi_in = a->seed[cur] + pl * (9 * ns + 8);
-        e = launch_add_planes(a->A.lphi_tot, lphi_in, (unsigned)(pl * ns), dev_grad_phi0, a->stream);
-        if (e != cudaSuccess) return adj_fail(a, e, "phi0 gradient");
+    if (a->graph) {
+        e = cudaGraphLaunch(a->graph, a->stream);
+        if (e != cudaSuccess) return adj_fail(a, e, "graph launch");
+    } else if ((e = adj_backward_body(a)) != cudaSuccess) {
+        return adj_fail(a, e, "reverse sweep");
     }
+    a->sim->launches += adj_sweep_launches(a);
+    if (dev_grad_phi0 &&
+        (e = cudaMemcpyAsync(dev_grad_phi0, a->grad_buf, pb * ns, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess)
+        return adj_fail(a, e, "phi0 gradient");
     double acc[kMaxPhases * kMaxPhases + 1];
-    if ((e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * c.contrib, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * (np + 1), cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(a->stream)) != cudaSuccess)
         return adj_fail(a, e, "gradient download");
+    (void)c;
     if (host_grad_sigma) {
         for (int i = 0; i < N * N; ++i) host_grad_sigma[i] = 0.0;
         int q = 0;
@@ -1245,27 +1315,16 @@ nlbm_status nlbm_adjoint_reverse_step(nlbm_adjoint *a, const float *dev_state, c
     const AdjCounts c = adj_counts(ns);
     cudaError_t e;
     if ((e = cudaMemcpyAsync(a->seed[0], dev_seed_out, pb * c.seedset, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(a->acc, 0, sizeof(double) * c.contrib, a->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(a->A.gacc, 0, pb * c.contrib, a->stream)) != cudaSuccess)
         return adj_fail(a, e, "seed");
-    AdjFields A = a->A;
-    float *so = a->seed[0], *si = a->seed[1];
-    A.lf_out = so;
-    A.lg_out = so + pl * 9 * ns;
-    A.lphi_out = A.lg_out + pl * 8;
-    A.lu_out = A.lphi_out + pl * ns;
-    A.lm_out = A.lu_out + pl * 2;
-    A.lf_in = si;
-    A.lg_in = si + pl * 9 * ns;
-    A.lphi_in = A.lg_in + pl * 8;
-    A.lu_in = A.lphi_in + pl * ns;
-    A.lm_in = A.lu_in + pl * 2;
     const StepParams kp = adj_params_from_state(a, dev_state);
-    if ((e = launch_reverse_step(ns, kp, a->T, A, a->partials, a->acc, a->stream)) != cudaSuccess)
+    if ((e = launch_reverse_step(ns, kp, a->T, adj_fields(a, a->seed[0], a->seed[1]), a->stream)) != cudaSuccess ||
+        (e = launch_grad_reduce(a->A.gacc, np + 1, (unsigned)pl, a->partials, a->acc, a->stream)) != cudaSuccess)
         return adj_fail(a, e, "reverse step");
     a->sim->launches += 9;
     double acc[kMaxPhases * kMaxPhases + 1];
-    if ((e = cudaMemcpyAsync(dev_seed_in, si, pb * c.seedset, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * c.contrib, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(dev_seed_in, a->seed[1], pb * c.seedset, cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(acc, a->acc, sizeof(double) * (np + 1), cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(a->stream)) != cudaSuccess)
         return adj_fail(a, e, "reverse step results");
     if (host_grad_sigma) {
@@ -1283,6 +1342,7 @@ int64_t nlbm_adjoint_kernel_launches(const nlbm_adjoint *a) { return a ? a->sim-
 void nlbm_adjoint_destroy(nlbm_adjoint *a)
 {
     if (!a) return;
+    if (a->graph) cudaGraphExecDestroy(a->graph);
     nlbm_destroy(a->sim);
     delete a;
 }

@@ -450,11 +450,16 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     float Mcx = 0.f, Mcy = 0.f, Mnx = 0.f, Mny = 0.f;   // m_phi(t)
     float Ucx = 0.f, Ucy = 0.f, Unx = 0.f, Uny = 0.f;   // u(t-1) of the own node
     float ub_x = 0.f, ub_y = 0.f;                       // u(t-1) for stage B of this iteration
+    float ub_s = 1.f;                                   // its sign: -1 on a no-slip ghost node
 
     for (int it = 0; it < TYe + 4; ++it) {
         const int ra = y0 - 2 + it;
         // stage-C inputs of row ra - 2, requested before stages A and B
+        // (loaded raw; anything computed from them waits until stage C, so
+        // that the loads overlap stages A and B)
         float g[9], php[NS], mpx = 0.f, mpy = 0.f;
+        float gps[9];             // 16-bit storage: P of the source node
+        unsigned short gq[9];     // 16-bit storage: stored deviation
         unsigned node = 0;
         const bool do_c = it >= 4 && own;
         if (do_c) {
@@ -467,10 +472,9 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                 if constexpr (ST == 0) {
                     g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
                 } else {
-                    // g_i = 3 w_i P(source) + stored deviation
                     const unsigned short *g16 = (const unsigned short *)P.gin;
-                    const float dev = Store16<ST>::dec(__ldg(g16 + (unsigned)(gdir[i] - 1) * pl + gnode[i]));
-                    g[i] = __fmaf_rn(3.f * w_of(i), __ldg(P.pin + gnode[i]), dev);
+                    gq[i] = __ldg(g16 + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
+                    gps[i] = __ldg(P.pin + gnode[i]);
                 }
             }
             node = (unsigned)y * nx + xg;
@@ -480,14 +484,16 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             mpy = P.mphi[pl + node];
         }
         // previous-step velocity of row ra, used by stage B of the next iteration
-        float ua_x = 0.f, ua_y = 0.f;
+        // (the ghost sign is applied where the value is used, so that no
+        // instruction here waits for these loads)
+        float ua_x = 0.f, ua_y = 0.f, ua_s = 1.f;
         if (in_ring && it >= 1 && it + 1 < TYe + 4) {
             bool yflip;
             const int yv = map_axis(ra, P.ny, P.wall_y, yflip);
             const unsigned k = (unsigned)yv * nx + xc;
             ua_x = __ldg(P.uin + k);
             ua_y = __ldg(P.uin + pl + k);
-            if (xflip != yflip) { ua_x = -ua_x; ua_y = -ua_y; }   // no-slip ghost
+            if (xflip != yflip) ua_s = -1.f;   // no-slip ghost: u = -u(image)
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this row's pulled f landed
         par_cur = par_next;
@@ -526,7 +532,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                 window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
                 source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
                 mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
-                s_w[s3 * T + t] = mx * ub_y - ub_x * my;
+                s_w[s3 * T + t] = ub_s * (mx * ub_y - ub_x * my);
 #pragma unroll
                 for (int p = 0; p < NS; ++p) { Rnx[p] = Rx[p]; Rny[p] = Ry[p]; }
                 Mnx = mx;
@@ -595,6 +601,11 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             }
 
             // macroscopic velocity (Eq. (25b)) and mass flux (Eq. (13))
+            if constexpr (ST != 0) {
+                // g_i = 3 w_i P(source) + stored deviation
+#pragma unroll
+                for (int i = 1; i < 9; ++i) g[i] = __fmaf_rn(3.f * w_of(i), gps[i], Store16<ST>::dec(gq[i]));
+            }
             const float sg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
             const float jgx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
             const float jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
@@ -752,6 +763,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
         Ucy = Uny;
         ub_x = ua_x;
         ub_y = ua_y;
+        ub_s = ua_s;
     }
 }
 
