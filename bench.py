@@ -333,8 +333,11 @@ def measure_adjoint(timed):
     ms_plain = timed(stream, plain.step, T) * T
     plain.close()
     run = AdjointRun(q, T, every)
-    run.forward(phi0)   # warm-up of both sweeps
-    run.backward(torch.zeros((N,) + phi0.shape[1:], device="cuda"))
+    # warm-up: the first reverse sweep of a handle loads the kernels and
+    # captures the sweep into a CUDA graph (about 0.5 s); time a replay
+    for _ in range(2):
+        run.forward(phi0)
+        run.backward(torch.zeros((N,) + phi0.shape[1:], device="cuda"))
     l0 = run.kernel_launches
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()

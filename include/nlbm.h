@@ -273,6 +273,74 @@ void nlbm_batch_destroy(nlbm_batch *b);
 /* Text of the ensemble's last error (b may be NULL: last failed create). */
 const char *nlbm_batch_last_error(const nlbm_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Adjoint: gradients of a loss of the final phase fields.
+ *
+ * For L(phi(T)) after T steps of the problem p from phi_0, the reverse sweep
+ * gives dL/dphi_0, dL/dsigma_pq (Eq. (15) tensions, through the chemical
+ * potentials of Eq. (17)) and dL/dM (through tau_f, Eq. (20), and m_phi,
+ * Eq. (13)).  Each step is reversed by rebuilding its intermediate fields
+ * from its input state and taking the adjoint through its stages in
+ * reverse order (collisions, Eqs. (18)-(24); force and macroscopic fields,
+ * Eqs. (16), (25); the Model B source, Eqs. (3)-(4); the stencils, Eq. (27);
+ * streaming); states are checkpointed every `checkpoint_every` steps and
+ * each segment is recomputed during the sweep.  Supported: Model B,
+ * periodic on both axes, FP32 storage (ENOTSUP otherwise).  Unit vectors
+ * should use the smooth reading (p->unit_delta > 0, e.g. 1e-3): with the
+ * thresholded one the step is not differentiable where v passes through 0.
+ * ------------------------------------------------------------------------ */
+typedef struct nlbm_adjoint nlbm_adjoint;
+
+/* Device workspace bytes for nsteps >= 1 steps with a checkpoint every
+ * checkpoint_every >= 1 steps: the simulation, ceil(nsteps / every)
+ * checkpoints and `every` segment states of 10(N-1)+12 floats a node, the
+ * adjoint fields.  Host only. */
+nlbm_status nlbm_adjoint_workspace_bytes(const nlbm_params *p, int32_t nsteps, int32_t checkpoint_every,
+                                         size_t *bytes);
+
+/* Create a differentiable run in caller-owned device memory (256-byte
+ * aligned, at least nlbm_adjoint_workspace_bytes()); cuda_stream as for
+ * nlbm_create(). */
+nlbm_status nlbm_adjoint_create(const nlbm_params *p, int32_t nsteps, int32_t checkpoint_every,
+                                void *dev_workspace, size_t workspace_bytes, void *cuda_stream,
+                                nlbm_adjoint **out);
+
+/* Run the nsteps forward steps from dev_phi0 [N-1][ny][nx] (as
+ * nlbm_set_phi()), storing the checkpoints; write phi(T) [N][ny][nx] into
+ * dev_phi_final if non-NULL.  Asynchronous. */
+nlbm_status nlbm_adjoint_forward(nlbm_adjoint *a, const float *dev_phi0, float *dev_phi_final);
+
+/* Reverse sweep after nlbm_adjoint_forward(): dev_seed [N][ny][nx] is
+ * dL/dphi(T) over all N phases (phase N = 1 - sum is folded in).  Writes
+ * dL/dphi_0 [N-1][ny][nx] into dev_grad_phi0 (may be NULL), dL/dsigma into
+ * host_grad_sigma [N*N] (symmetric: entry (p, q) is the derivative with
+ * respect to the pair's single value; may be NULL) and dL/dM into
+ * *host_grad_mobility (may be NULL).  The sweep is the same launch sequence
+ * on every call of a handle: on a stream other than the legacy default one,
+ * the first call captures it into a CUDA graph (kernel loading and capture
+ * take a while once) and later calls replay it.  Synchronizes. */
+nlbm_status nlbm_adjoint_backward(nlbm_adjoint *a, const float *dev_seed, float *dev_grad_phi0,
+                                  double *host_grad_sigma, double *host_grad_mobility);
+
+/* One reverse step on its own, for losses spread over time: dev_state is a
+ * step's input state [f 9(N-1), g 8, u 2, phi N-1, m_phi 2 planes] (the
+ * first planes of an nlbm_save() checkpoint), dev_seed_out the adjoint of
+ * its outputs [f 9(N-1), g 8, phi N-1, u 2, m_phi 2 planes]; writes the
+ * adjoint of its inputs in the seed layout to dev_seed_in and this step's
+ * parameter gradients to the host arrays (as nlbm_adjoint_backward()).
+ * Synchronizes. */
+nlbm_status nlbm_adjoint_reverse_step(nlbm_adjoint *a, const float *dev_state, const float *dev_seed_out,
+                                      float *dev_seed_in, double *host_grad_sigma, double *host_grad_mobility);
+
+/* 1 when the reverse sweep of this handle replays a captured graph. */
+int32_t nlbm_adjoint_uses_graph(const nlbm_adjoint *a);
+/* Kernels launched by the handle (forward, recompute and reverse). */
+int64_t nlbm_adjoint_kernel_launches(const nlbm_adjoint *a);
+/* Release the handle (not the workspace).  Safe on NULL. */
+void nlbm_adjoint_destroy(nlbm_adjoint *a);
+/* Text of the handle's last error (a may be NULL: last failed create). */
+const char *nlbm_adjoint_last_error(const nlbm_adjoint *a);
+
 /* Release the handle (not the workspace).  Safe on NULL.  Does not wait for
  * enqueued work; synchronize first if the workspace is to be reused. */
 void nlbm_destroy(nlbm_sim *s);

@@ -1337,6 +1337,8 @@ nlbm_status nlbm_adjoint_reverse_step(nlbm_adjoint *a, const float *dev_state, c
     return NLBM_OK;
 }
 
+int32_t nlbm_adjoint_uses_graph(const nlbm_adjoint *a) { return a && a->graph ? 1 : 0; }
+
 int64_t nlbm_adjoint_kernel_launches(const nlbm_adjoint *a) { return a ? a->sim->launches : -1; }
 
 void nlbm_adjoint_destroy(nlbm_adjoint *a)

@@ -448,6 +448,12 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 #pragma unroll
     for (int p = 0; p < NS; ++p) { Rcx[p] = Rcy[p] = Rnx[p] = Rny[p] = 0.f; }
     float Mcx = 0.f, Mcy = 0.f, Mnx = 0.f, Mny = 0.f;   // m_phi(t)
+    // FP32 storage: phi, grad phi and lap phi of the row stage B evaluated
+    // (Eq. (27)); stage C of the same row reuses them instead of reading the
+    // window again (16-bit storage reads the window there anyway)
+    float PHc[NS], GXc[NS], GYc[NS], LPc[NS], PHn[NS], GXn[NS], GYn[NS], LPn[NS];
+#pragma unroll
+    for (int p = 0; p < NS; ++p) PHc[p] = GXc[p] = GYc[p] = LPc[p] = PHn[p] = GXn[p] = GYn[p] = LPn[p] = 0.f;
     float Ucx = 0.f, Ucy = 0.f, Unx = 0.f, Uny = 0.f;   // u(t-1) of the own node
     float ub_x = 0.f, ub_y = 0.f;                       // u(t-1) for stage B of this iteration
     float ub_s = 1.f;                                   // its sign: -1 on a no-slip ghost node
@@ -529,7 +535,14 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             const int s3 = slot3(rb);
             if (in_flux) {
                 float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
-                window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
+                if constexpr (ST == 0) {
+                    float lap[N];
+                    window_grad_lap<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy, lap);
+#pragma unroll
+                    for (int p = 0; p < NS; ++p) { PHn[p] = ph[p]; GXn[p] = gx[p]; GYn[p] = gy[p]; LPn[p] = lap[p]; }
+                } else {
+                    window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
+                }
                 source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
                 mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
                 s_w[s3 * T + t] = ub_s * (mx * ub_y - ub_x * my);
@@ -547,7 +560,26 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             const int y = ra - 2;
             const int sm = slot5(y - 1), s0 = slot5(y), sp = slot5(y + 1);
             float ph[N], gx[N], gy[N], lap[N];
-            window_grad_lap<NS>(s_phi, T, sm, s0, sp, t, ph, gx, gy, lap);
+            if constexpr (ST == 0) {
+                float sph = 0.f, sgx = 0.f, sgy = 0.f, sl = 0.f;
+#pragma unroll
+                for (int p = 0; p < NS; ++p) {
+                    ph[p] = PHc[p];
+                    gx[p] = GXc[p];
+                    gy[p] = GYc[p];
+                    lap[p] = LPc[p];
+                    sph += ph[p];
+                    sgx += gx[p];
+                    sgy += gy[p];
+                    sl += lap[p];
+                }
+                ph[NS] = 1.f - sph;
+                gx[NS] = -sgx;
+                gy[NS] = -sgy;
+                lap[NS] = -sl;
+            } else {
+                window_grad_lap<NS>(s_phi, T, sm, s0, sp, t, ph, gx, gy, lap);
+            }
 
             // mixture density, viscosity and grad rho (Eqs. (11),(12))
             float rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f;
@@ -756,7 +788,14 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             if (P.pout) P.pout[node] = Pr;
         }
 #pragma unroll
-        for (int p = 0; p < NS; ++p) { Rcx[p] = Rnx[p]; Rcy[p] = Rny[p]; }
+        for (int p = 0; p < NS; ++p) {
+            Rcx[p] = Rnx[p];
+            Rcy[p] = Rny[p];
+            PHc[p] = PHn[p];
+            GXc[p] = GXn[p];
+            GYc[p] = GYn[p];
+            LPc[p] = LPn[p];
+        }
         Mcx = Mnx;
         Mcy = Mny;
         Ucx = Unx;
@@ -768,7 +807,10 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 }
 
 template <int NS, int MODEL, int T, int ST>
-__global__ void __launch_bounds__(T, ST == 0 ? 0 : 512 / T) step_kernel(const StepParams P, const int TY)
+// FP32: three blocks of 128 threads per SM, up to 170 registers a thread
+// (measured: the throughput is flat between 12 and 16 resident warps and
+// falls when the registers are squeezed to fit more).  16-bit storage: four.
+__global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T) step_kernel(const StepParams P, const int TY)
 {
     extern __shared__ float smem[];
     step_tile<NS, MODEL, T, ST>(P, blockIdx.x * (T - 4), blockIdx.y * TY, TY, smem);

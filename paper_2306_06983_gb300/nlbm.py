@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "nlbm_adjoint_forward": (st, [vp, vp, vp]),
         "nlbm_adjoint_backward": (st, [vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]),
         "nlbm_adjoint_kernel_launches": (ctypes.c_int64, [vp]),
+        "nlbm_adjoint_uses_graph": (ctypes.c_int32, [vp]),
         "nlbm_adjoint_reverse_step": (st, [vp, vp, vp, vp, P(ctypes.c_double), P(ctypes.c_double)]),
         "nlbm_adjoint_destroy": (None, [vp]),
         "nlbm_adjoint_last_error": (ctypes.c_char_p, [vp]),
@@ -646,6 +647,10 @@ class AdjointRun:
     @property
     def kernel_launches(self) -> int:
         return nlbm_adjoint_kernel_launches(self.h)
+
+    @property
+    def uses_graph(self) -> bool:
+        return bool(load_library().nlbm_adjoint_uses_graph(self.h))
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

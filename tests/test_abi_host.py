@@ -27,6 +27,22 @@ def test_every_declared_symbol_is_exported(lib):
         assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
 
 
+def test_every_exported_symbol_is_declared(lib):
+    """The converse: no extern "C" entry point of the library is missing
+    from include/nlbm.h (read with nm when the host has it)."""
+    import shutil
+    import subprocess
+    from paper_2306_06983_gb300 import nlbm
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-D", "--defined-only", nlbm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines()
+                if line.split() and line.split()[-1].startswith("nlbm_")}
+    assert exported, "no nlbm_ symbols found"
+    missing = sorted(exported - set(nlbm.declared_symbols()))
+    assert not missing, missing
+
+
 def test_status_strings(lib):
     from paper_2306_06983_gb300 import nlbm
     assert nlbm.nlbm_status_string(0) == "ok"
