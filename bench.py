@@ -306,7 +306,8 @@ def measure_adjoint(timed):
     phi_hat|^2 with phi_hat from sigma = (0.012, 0.008, 0.010); gradients with
     respect to the three tensions, the mobility and the initial fields from
     sigma = (0.01, 0.01, 0.01).  Forward (with checkpoints) and reverse sweep
-    timed with CUDA events; a plain forward of the same steps beside them."""
+    timed with CUDA events (median of three calls after two warm-up calls);
+    a plain forward of the same steps beside them."""
     import torch
     from paper_2306_06983_gb300 import workloads as W
     from paper_2306_06983_gb300.nlbm import AdjointRun, Simulation, pair_list
@@ -334,23 +335,29 @@ def measure_adjoint(timed):
     plain.close()
     run = AdjointRun(q, T, every)
     # warm-up: the first reverse sweep of a handle loads the kernels and
-    # captures the sweep into a CUDA graph (about 0.5 s); time a replay
+    # captures the sweep into a CUDA graph (about 0.5 s), and the seed's
+    # subtraction loads torch's own kernel; time replays
     for _ in range(2):
-        run.forward(phi0)
-        run.backward(torch.zeros((N,) + phi0.shape[1:], device="cuda"))
+        phiT = run.forward(phi0)
+        run.backward((phiT - tgt).contiguous())
     l0 = run.kernel_launches
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    torch.cuda.synchronize()
-    e[0].record(stream)
-    phiT = run.forward(phi0)
-    e[1].record(stream)
-    seed = (phiT - tgt).contiguous()
-    g0, gs, gm = run.backward(seed)
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    launches = run.kernel_launches - l0
+    fwds, bwds = [], []
+    for _ in range(3):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        phiT = run.forward(phi0)
+        e[1].record(stream)
+        seed = (phiT - tgt).contiguous()
+        g0, gs, gm = run.backward(seed)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwds.append(e[0].elapsed_time(e[1]))
+        bwds.append(e[1].elapsed_time(e[2]))
+    launches = (run.kernel_launches - l0) // 3
+    graph = run.uses_graph
     run.close()
-    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    fwd, bwd = float(np.median(fwds)), float(np.median(bwds))
     nodes = 256 * 256
     return {
         "workload": "256x256 periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
@@ -358,6 +365,7 @@ def measure_adjoint(timed):
         "value": round(nodes * T / ((fwd + bwd) / 1e3) / 1e6, 2), "unit": "MLUPS (differentiated)",
         "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3), "backward_over_forward": round(bwd / fwd, 2),
         "plain_forward_ms": round(ms_plain, 3), "gpu_launches": launches,
+        "backward_ms_calls": [round(v, 3) for v in bwds], "reverse_sweep_graph": graph,
         "loss": float(0.5 * ((phiT.double() - tgt.double()) ** 2).sum()),
         "grad_sigma_pairs": [float(gs[a, b]) for a, b in pair_list(N)], "grad_mobility": float(gm),
         "grad_phi0_max_abs": float(g0.abs().max()),
