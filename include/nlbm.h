@@ -169,9 +169,10 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s);
 
 /* Tile of the fused step kernel: tx threads per block (64, 128 or 256; one
  * thread per column, each block updating a strip of tx - 4 columns) marching
- * down ty rows (>= 1), or ty = 0 (the default) to let the library pick the
- * march length that fills the GPU with one wave of blocks.  EINVAL outside
- * those values.  Takes effect on the next nlbm_step(). */
+ * down ty rows (>= 1), or ty = 0 (the default) to let the library cut every
+ * strip into equal row chunks (at least 16 rows) so that the grid is one
+ * wave of resident blocks.  EINVAL outside those values.  Takes effect on
+ * the next nlbm_step(). */
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
 nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
 

@@ -6,9 +6,10 @@
 // exactly the resident blocks of the device takes tiles in table order from
 // a global counter and runs the same fused step (step_tile) on each, with the
 // tile's parameter block copied into shared memory.  Model A and Model B
-// simulations share the launch (the model is read per tile).  Simulations
-// never exchange data, so no block waits on another; the only cross-block
-// traffic is the tile counter.
+// simulations share the launch (the model is read per tile), and so do
+// simulations whose pulls are staged as row windows and those that are not.
+// Simulations never exchange data, so no block waits on another; the only
+// cross-block traffic is the tile counter.
 #include "step_kernel.cuh"
 
 namespace nlbm {
@@ -18,7 +19,7 @@ __global__ void __launch_bounds__(T) batch_step_kernel(const StepParams *__restr
                                                         const BatchTile *__restrict__ tiles, int ntiles,
                                                         int *counters, int parity)
 {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     __shared__ StepParams s_P;
     __shared__ int s_k;
     // the other counter is the next launch's; this launch's was cleared by
@@ -34,10 +35,17 @@ __global__ void __launch_bounds__(T) batch_step_kernel(const StepParams *__restr
         int *dst = reinterpret_cast<int *>(&s_P);
         for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / sizeof(int)); i += T) dst[i] = src[i];
         __syncthreads();
-        if (s_P.model == 0)
-            step_tile<NS, 0, T, 0>(s_P, tl.x0, tl.y0, tl.ty, smem);
-        else
-            step_tile<NS, 1, T, 0>(s_P, tl.x0, tl.y0, tl.ty, smem);
+        if (s_P.row_window) {
+            if (s_P.model == 0)
+                step_tile<NS, 0, T, 0, true>(s_P, tl.x0, tl.y0, tl.ty, smem);
+            else
+                step_tile<NS, 1, T, 0, true>(s_P, tl.x0, tl.y0, tl.ty, smem);
+        } else {
+            if (s_P.model == 0)
+                step_tile<NS, 0, T, 0, false>(s_P, tl.x0, tl.y0, tl.ty, smem);
+            else
+                step_tile<NS, 1, T, 0, false>(s_P, tl.x0, tl.y0, tl.ty, smem);
+        }
         __syncthreads();   // s_k, s_P and the rings are reused by the next tile
     }
 }
@@ -48,7 +56,7 @@ template <int NS, int T>
 cudaError_t configure(int *blocks)
 {
     static_assert(sizeof(StepParams) % sizeof(int) == 0, "parameter block copied as ints");
-    const size_t smem = step_smem_bytes<NS, T, 0>();
+    const size_t smem = step_smem_bytes<NS, T, 0, true>();
     static int configured[64] = {0};
     static int resident[64] = {0};
     int dev = 0;
@@ -78,7 +86,7 @@ cudaError_t launch_nt(const StepParams *d_params, const BatchTile *d_tiles, int 
     cudaError_t e = configure<NS, T>(&blocks);
     if (e != cudaSuccess) return e;
     const int grid = ntiles < blocks ? (ntiles > 0 ? ntiles : 1) : blocks;
-    batch_step_kernel<NS, T><<<grid, T, step_smem_bytes<NS, T, 0>(), st>>>(d_params, d_tiles, ntiles,
+    batch_step_kernel<NS, T><<<grid, T, step_smem_bytes<NS, T, 0, true>(), st>>>(d_params, d_tiles, ntiles,
                                                                          d_counters, parity);
     return cudaGetLastError();
 }

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <algorithm>
 #include <new>
@@ -612,6 +613,9 @@ nlbm_status upload_params(nlbm_batch *b)
     for (int par = 0; par < 2; ++par)
         for (int k = 0; k < b->count; ++k) {
             StepParams kp = step_params(b->sims[k], par, par ^ 1);
+            // the same condition as the single-simulation launcher's
+            kp.row_window = !kp.wall_x && kp.nx % 4 == 0 &&
+                            ((reinterpret_cast<uintptr_t>(kp.fin) | reinterpret_cast<uintptr_t>(kp.gin)) & 15) == 0;
             kp.pout = nullptr;
             h[(size_t)(2 * par) * b->count + k] = kp;
             kp.pout = b->sims[k]->P(0);

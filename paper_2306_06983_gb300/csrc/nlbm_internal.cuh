@@ -63,6 +63,7 @@ struct StepParams {
     float *mphi;               // [2][plane] in: previous step, out: this step
     float *pout;               // [plane] or nullptr
     int model;                 // 0 Model A, 1 Model B (read by the ensemble kernel)
+    int row_window;            // ensemble kernel: stage pulls as row windows (see step_tile)
 };
 
 // One work item of the ensemble kernel: the strip of simulation `sim` that

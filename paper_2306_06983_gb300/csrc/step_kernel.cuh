@@ -57,7 +57,6 @@ __device__ __forceinline__ int map_axis(int c, int n, int wall, bool &flip)
 
 __device__ __forceinline__ int slot5(int r) { return (r + 10) % 5; }
 __device__ __forceinline__ int slot3(int r) { return (r + 9) % 3; }
-__device__ __forceinline__ int slot2(int r) { return (r + 8) & 1; }
 
 // Sources of the pull at node (x, y): direction i of this node comes from
 // node[i] in plane dir[i] (dir[i] = i, or the opposite direction of the own
@@ -103,9 +102,11 @@ __device__ __forceinline__ void cp_async4(float *dst_smem, const float *src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one()
+// 16-byte copy (both addresses 16-byte aligned), cached in L2 only.
+__device__ __forceinline__ void cp_async16(float *dst_smem, const float *src)
 {
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
 // Start the copies of the 9 (N-1) populations node (x, y) pulls into column
@@ -145,6 +146,129 @@ __device__ __forceinline__ void sum_pulled(const float *s_F, int WF, int col, fl
         for (int i = 1; i < 9; ++i) {
             const float t = s + f[i];
             if (OWN) e += f[i] - (t - s);     // Fast2Sum error term
+            s = t;
+        }
+        ph[p] = s;
+        if (OWN) {
+            plo[p] = e;
+            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        }
+    }
+}
+
+// Row windows (FP32 storage, nx a multiple of 4, no wall across x).  Each
+// warp stages the rows its 32 ring columns pull from: for every population
+// plane, a window of kWin columns that starts 4 columns left of the warp's
+// first node (so that it is 16-byte aligned) and covers the one-column halo
+// on both sides.  Lanes 0..26 copy it in 16-byte pieces, lane 9 g + c taking
+// piece c of the three directions of group g (group_dir); lane l then finds
+// f_i(x - c_i) at window column 2 + l - c_ix.  Only the warp's own lanes
+// read its windows, so a warp barrier orders copies and reads.
+constexpr int kWin = 36;
+
+// Direction k (0..2) of group g: g = 0 the directions with c_iy = 0
+// {0, 1, 3}, g = 1 those with c_iy = +1 {2, 5, 6}, g = 2 those with
+// c_iy = -1 {4, 7, 8}; groups 1 and 2 are each other's opposites in order.
+__device__ __forceinline__ int group_dir(int g, int k)
+{
+    if (k == 0) return 2 * g;
+    if (k == 1) return g == 0 ? 1 : (g == 1 ? 5 : 7);
+    return g == 0 ? 3 : (g == 1 ? 6 : 8);
+}
+
+// Source row of group g for nodes of row y in [0, ny): row y - c_iy
+// (wrapped on a periodic axis), or, when that row is across a half-way wall,
+// row y itself with the opposite directions (the link is bounced back).
+__device__ __forceinline__ void group_source(const StepParams &P, int y, int g, int &geff, unsigned &row)
+{
+    int ys = y - (g == 0 ? 0 : (g == 1 ? 1 : -1));
+    geff = g;
+    if (ys < 0 || ys >= P.ny) {
+        if (P.wall_y) {
+            ys = y;
+            geff = 3 - g;
+        } else {
+            ys += ys < 0 ? P.ny : -P.ny;
+        }
+    }
+    row = (unsigned)ys * (unsigned)P.nx;
+}
+
+// Start the copies of the phase-population windows node row y pulls:
+// window slot 9 p + i of the warp holds what f_i of phase p pulls.
+template <int NS>
+__device__ __forceinline__ void stage_pull_rows(const StepParams &P, int y, int g, int wc, unsigned wcol,
+                                                float *s_Fw)
+{
+    int ge;
+    unsigned row;
+    group_source(P, y, g, ge, row);
+    const float *base = P.fin + (row + wcol);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const unsigned off = (unsigned)group_dir(ge, k) * P.plane;
+        float *dst = s_Fw + group_dir(g, k) * kWin + 4 * wc;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) cp_async16(dst + 9 * p * kWin, base + (size_t)p * 9 * P.plane + off);
+    }
+}
+
+// The same for the flow populations g_1..g_8 (window slot i - 1).
+__device__ __forceinline__ void stage_flow_rows(const StepParams &P, int y, int g, int wc, unsigned wcol,
+                                                float *s_Gw)
+{
+    int ge;
+    unsigned row;
+    group_source(P, y, g, ge, row);
+    const float *base = P.gin + (row + wcol);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (g == 0 && k == 0) continue;   // g_0 is not stored
+        cp_async16(s_Gw + (group_dir(g, k) - 1) * kWin + 4 * wc,
+                   base + (unsigned)(group_dir(ge, k) - 1) * P.plane);
+    }
+}
+
+// Window columns lane l reads f_i (or g_i) at for a node row whose links
+// with c_iy = +1 (bl) or c_iy = -1 (bh) are bounced back at a y wall.
+struct WinCols {
+    int b, c5, c6, c7, c8;   // c_0..c_4 follow from b: b, b - 1, b, b + 1, b
+};
+__device__ __forceinline__ WinCols win_cols(int lane, bool bl, bool bh)
+{
+    WinCols w;
+    w.b = 2 + lane;
+    w.c5 = bl ? w.b : w.b - 1;
+    w.c6 = bl ? w.b : w.b + 1;
+    w.c7 = bh ? w.b : w.b + 1;
+    w.c8 = bh ? w.b : w.b - 1;
+    return w;
+}
+
+// sum_pulled from the warp's windows.
+template <int NS, bool OWN>
+__device__ __forceinline__ void sum_pulled_win(const float *s_Fw, const WinCols &c, float (&ph)[NS],
+                                               float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
+{
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float *w = s_Fw + 9 * p * kWin;
+        float f[9];
+        f[0] = w[c.b];
+        f[1] = w[kWin + c.b - 1];
+        f[2] = w[2 * kWin + c.b];
+        f[3] = w[3 * kWin + c.b + 1];
+        f[4] = w[4 * kWin + c.b];
+        f[5] = w[5 * kWin + c.c5];
+        f[6] = w[6 * kWin + c.c6];
+        f[7] = w[7 * kWin + c.c7];
+        f[8] = w[8 * kWin + c.c8];
+        float s = f[0], e = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float t = s + f[i];
+            if (OWN) e += f[i] - (t - s);
             s = t;
         }
         ph[p] = s;
@@ -400,11 +524,15 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
 
 // One tile of the fused step: the strip of columns [x0, x0 + T - 4) marching
 // rows [y0, y0 + TY) of the simulation described by P.  smem is the dynamic
-// shared memory of the block (launch_step_nst gives its size).
-template <int NS, int MODEL, int T, int ST>
+// shared memory of the block (step_smem_bytes gives its size).  VEC: the
+// pulled populations are staged as row windows (FP32 storage, nx a multiple
+// of 4, 16-byte aligned planes, no wall across x); otherwise every ring
+// thread copies the nine values its node pulls, 4 bytes at a time.
+template <int NS, int MODEL, int T, int ST, bool VEC = false>
 __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, const int y0, const int TY,
                                           float *smem)
 {
+    static_assert(!VEC || ST == 0, "row windows stage FP32 populations");
     constexpr int N = NS + 1;
     // Thread t owns ring column t, lattice column x0 - 2 + t: every thread
     // pulls one phase field in stage A, the inner T - 2 compute m_phi in
@@ -415,7 +543,9 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     float *s_w = s_phi + 5 * NS * T;         // [3][T]       w = m_phi,x u_y - u_x m_phi,y, rows r-1..r+1
     float *s_j = s_w + 3 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
     float *s_F = s_j + 9 * NS * T;           // [9NS][T]     staged pulled f of the next row
-                                             // ([10NS][T] with 16-bit storage, see prefetch_pull16)
+                                             // ([10NS][T] with 16-bit storage, see prefetch_pull16;
+                                             // VEC: [T/32][9NS][kWin] row windows)
+    float *s_G = s_F + (T / 32) * 9 * NS * kWin;   // VEC: [2][T/32][8][kWin] g windows of two rows
 
     const int t = threadIdx.x;
     const int We = min(W, P.nx - x0), TYe = min(TY, P.ny - y0);
@@ -429,13 +559,28 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     const int xg = x0 - 2 + t;                   // lattice x of an own node
 
     unsigned par_next = 0, par_cur = 0;   // halves of the staged 16-bit words
-    // The pulled populations of row r+1 are copied into this thread's
-    // staging slots (cp.async) while rows r..r-2 are computed; each thread
-    // only reads the slots it filled itself.
+    // VEC: this lane's window piece and direction group, the (wrapped)
+    // lattice column of that piece, and the warp's windows.
+    const int lane = t & 31, wc = lane % 9, wg = lane / 9;
+    const bool copier = VEC && lane < 27 && 32 * (t >> 5) < We + 4;
+    unsigned wcol = 0;
+    if constexpr (VEC) {
+        int c = x0 - 4 + 32 * (t >> 5) + 4 * wc;
+        if (c < 0 || c >= nx) c = ((c % nx) + nx) % nx;   // periodic x: a piece never straddles the edge
+        wcol = (unsigned)c;
+    }
+    float *s_Fw = s_F + (t >> 5) * 9 * NS * kWin;
+    float *s_Gw = s_G + (t >> 5) * 8 * kWin;   // + (row & 1) * (T / 32) * 8 * kWin
+    // The pulled populations of row r+1 are copied into shared memory
+    // (cp.async) while rows r..r-2 are computed.  Without VEC each thread
+    // only reads the slots it filled itself; with VEC the warp barrier after
+    // the wait makes the warp's windows visible to all its lanes.
     {
         bool yflip;
         const int ya = map_axis(y0 - 2, P.ny, P.wall_y, yflip);
-        if (in_ring) {
+        if constexpr (VEC) {
+            if (copier) stage_pull_rows<NS>(P, ya, wg, wc, wcol, s_Fw);
+        } else if (in_ring) {
             if constexpr (ST == 0) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
             else par_next = prefetch_pull16<NS>(P, xc, ya, s_F, T, t);
         }
@@ -472,10 +617,12 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             const int y = ra - 2;
             unsigned gnode[9];
             int gdir[9];
-            pull_sources(P, xg, y, gnode, gdir);
+            if constexpr (!VEC) pull_sources(P, xg, y, gnode, gdir);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                if constexpr (ST == 0) {
+                if constexpr (VEC) {
+                    // staged as a row window, read in stage C
+                } else if constexpr (ST == 0) {
                     g[i] = __ldg(P.gin + (unsigned)(gdir[i] - 1) * pl + gnode[i]);
                 } else {
                     const unsigned short *g16 = (const unsigned short *)P.gin;
@@ -502,12 +649,21 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             if (xflip != yflip) ua_s = -1.f;   // no-slip ghost: u = -u(image)
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this row's pulled f landed
+        if constexpr (VEC) __syncwarp();
         par_cur = par_next;
         // ---------------------------------------------------- stage A
         if (in_ring) {
             float ph[NS], plo[NS], jx[NS], jy[NS];
-            if constexpr (ST == 0) sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
-            else sum_pulled16<NS, ST, true>(s_F, T, t, par_cur, ph, plo, jx, jy);
+            if constexpr (VEC) {
+                bool yflip;
+                const int yi = map_axis(ra, P.ny, P.wall_y, yflip);
+                const WinCols wcl = win_cols(lane, P.wall_y && yi == 0, P.wall_y && yi == P.ny - 1);
+                sum_pulled_win<NS, true>(s_Fw, wcl, ph, plo, jx, jy);
+            } else if constexpr (ST == 0) {
+                sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
+            } else {
+                sum_pulled16<NS, ST, true>(s_F, T, t, par_cur, ph, plo, jx, jy);
+            }
             const int s5 = slot5(ra);
 #pragma unroll
             for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
@@ -520,11 +676,24 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                     s_j[(s3 * 3 * NS + 3 * p + 2) * T + t] = plo[p];
                 }
             }
-            if (it + 1 < TYe + 4) {
+            if (!VEC && it + 1 < TYe + 4) {
                 bool yflip;
                 const int yn = map_axis(ra + 1, P.ny, P.wall_y, yflip);
                 if constexpr (ST == 0) prefetch_pull<NS>(P, xc, yn, s_F, T, t);
                 else par_next = prefetch_pull16<NS>(P, xc, yn, s_F, T, t);
+            }
+        }
+        if constexpr (VEC) {
+            __syncwarp();   // every lane of the warp has read its windows of row ra
+            if (copier) {
+                if (it + 1 < TYe + 4) {
+                    bool yflip;
+                    stage_pull_rows<NS>(P, map_axis(ra + 1, P.ny, P.wall_y, yflip), wg, wc, wcol, s_Fw);
+                }
+                // g of the row stage C completes next iteration
+                const int yg = ra - 1;
+                if (it >= 3 && yg < y0 + TYe)
+                    stage_flow_rows(P, yg, wg, wc, wcol, s_Gw + (yg & 1) * (T / 32) * 8 * kWin);
             }
         }
         cp_async_commit();
@@ -633,6 +802,18 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             }
 
             // macroscopic velocity (Eq. (25b)) and mass flux (Eq. (13))
+            if constexpr (VEC) {
+                const float *gw = s_Gw + (y & 1) * (T / 32) * 8 * kWin;
+                const WinCols wcl = win_cols(lane, P.wall_y && y == 0, P.wall_y && y == P.ny - 1);
+                g[1] = gw[wcl.b - 1];
+                g[2] = gw[kWin + wcl.b];
+                g[3] = gw[2 * kWin + wcl.b + 1];
+                g[4] = gw[3 * kWin + wcl.b];
+                g[5] = gw[4 * kWin + wcl.c5];
+                g[6] = gw[5 * kWin + wcl.c6];
+                g[7] = gw[6 * kWin + wcl.c7];
+                g[8] = gw[7 * kWin + wcl.c8];
+            }
             if constexpr (ST != 0) {
                 // g_i = 3 w_i P(source) + stored deviation
 #pragma unroll
@@ -806,62 +987,110 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     }
 }
 
-template <int NS, int MODEL, int T, int ST>
+// Grid: one block per (strip, row chunk), strips of T - 4 columns, strip
+// index fastest.  TY > 0: chunks of TY rows; TY = 0: chunk k of `chunks`
+// covers rows [k ny / chunks, (k + 1) ny / chunks).
+template <int NS, int MODEL, int T, int ST, bool VEC>
 // FP32: three blocks of 128 threads per SM, up to 170 registers a thread
 // (measured: the throughput is flat between 12 and 16 resident warps and
 // falls when the registers are squeezed to fit more).  16-bit storage: four.
-__global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T) step_kernel(const StepParams P, const int TY)
+__global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
+    step_kernel(const StepParams P, const int TY, const int chunks, const int strips)
 {
-    extern __shared__ float smem[];
-    step_tile<NS, MODEL, T, ST>(P, blockIdx.x * (T - 4), blockIdx.y * TY, TY, smem);
+    extern __shared__ __align__(16) float smem[];
+    const int s = blockIdx.x % strips, k = blockIdx.x / strips;
+    int y0, ty;
+    if (TY > 0) {
+        y0 = k * TY;
+        ty = TY;
+    } else {
+        y0 = (int)((long long)k * P.ny / chunks);
+        ty = (int)((long long)(k + 1) * P.ny / chunks) - y0;
+    }
+    if (ty <= 0 || y0 >= P.ny) return;
+    step_tile<NS, MODEL, T, ST, VEC>(P, s * (T - 4), y0, ty, smem);
 }
 
 // Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
-// the staging rows (9 slots per phase, 10 with 16-bit storage).
-template <int NS, int T, int ST>
+// the staging rows (9 slots per phase, 10 with 16-bit storage; VEC: the
+// warps' f windows and two rows of g windows).
+template <int NS, int T, int ST, bool VEC = false>
 constexpr size_t step_smem_bytes()
 {
+    if (VEC) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
     return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
 }
 
+// Resident blocks of one kernel variant on device dev (the dynamic
+// shared-memory limit, a per-device function attribute, is set on first use).
+template <int NS, int MODEL, int T, int ST, bool VEC>
+cudaError_t variant_slots(int dev, int *out)
+{
+    constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
+    static int slots[64] = {0};
+    if (!slots[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST, VEC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T, ST, VEC>, T, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        slots[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+    }
+    *out = slots[dev];
+    return cudaSuccess;
+}
+
+template <int NS, int MODEL, int T, int ST, bool VEC>
+cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStream_t st)
+{
+    constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
+    const int strips = (p.nx + T - 5) / (T - 4);
+    int chunks;
+    if (ty > 0) {
+        chunks = (p.ny + ty - 1) / ty;
+    } else {
+        // Automatic march length: as many row chunks per strip as there are
+        // resident-block slots per strip (one full wave), chunks of at least
+        // 16 rows.  Every chunk, of a narrow last strip too, gets the same
+        // rows: a block's time per row hardly depends on how many of its
+        // warps hold ring columns.
+        chunks = nslots / strips;
+        const int maxc = p.ny / 16 > 1 ? p.ny / 16 : 1;
+        if (chunks > maxc) chunks = maxc;
+        if (chunks < 1) chunks = 1;
+        ty = 0;
+    }
+    const long long blocks = (long long)strips * chunks;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    step_kernel<NS, MODEL, T, ST, VEC><<<(unsigned)blocks, T, smem, st>>>(p, ty, chunks, strips);
+    return cudaGetLastError();
+}
+
+// Row windows need FP32 storage, nx a multiple of 4 (rows and planes start
+// on 16-byte boundaries), 16-byte aligned population arrays and no wall
+// across x (a wall bounces single columns back, which a window cannot
+// express); they are used unless their larger shared memory would leave
+// fewer blocks resident.
 template <int NS, int MODEL, int T, int ST>
 cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
-    constexpr int tx = T;
-    const size_t smem = step_smem_bytes<NS, T, ST>();
-    // The dynamic shared-memory limit is a per-device function attribute.
-    static int configured_bytes[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if ((int)smem > configured_bytes[dev]) {
-        e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_bytes[dev] = (int)smem;
+    int plain = 0;
+    if ((e = variant_slots<NS, MODEL, T, ST, false>(dev, &plain)) != cudaSuccess) return e;
+    if constexpr (ST == 0) {
+        const bool vec = !p.wall_x && p.nx % 4 == 0 &&
+                         ((reinterpret_cast<uintptr_t>(p.fin) | reinterpret_cast<uintptr_t>(p.gin)) & 15) == 0;
+        int win = 0;
+        if (vec && (e = variant_slots<NS, MODEL, T, ST, true>(dev, &win)) != cudaSuccess) return e;
+        if (vec && win >= plain) return launch_step_variant<NS, MODEL, T, ST, true>(p, ty, win, st);
     }
-    if (ty <= 0) {
-        // Automatic march length: as many row chunks per strip as there are
-        // resident-block slots per strip, so the grid is one full wave.
-        static int cached_slots[64] = {0};
-        if (!cached_slots[dev]) {
-            int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T, ST>, tx, smem);
-            if (e != cudaSuccess) return e;
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            cached_slots[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
-        }
-        const int strips = (p.nx + tx - 5) / (tx - 4);
-        const int chunks = cached_slots[dev] / strips > 0 ? cached_slots[dev] / strips : 1;
-        ty = (p.ny + chunks - 1) / chunks;
-        if (ty < 16) ty = 16;
-    }
-    if (ty < (p.ny + 65534) / 65535) ty = (p.ny + 65534) / 65535;   // grid.y limit
-    dim3 grid((p.nx + tx - 5) / (tx - 4), (p.ny + ty - 1) / ty);
-    step_kernel<NS, MODEL, T, ST><<<grid, tx, smem, st>>>(p, ty);
-    return cudaGetLastError();
+    return launch_step_variant<NS, MODEL, T, ST, false>(p, ty, plain, st);
 }
 
 template <int NS, int MODEL, int ST>

@@ -75,6 +75,7 @@ CASES = {
     "ragged67x45_N4_A_walls": lambda: W.random_smooth(67, 45, 4, seed=4, model="A", model_a_n=1.5,
                                                       wall_x=True, wall_y=True),
     "ragged45x67_N2_B_wally": lambda: W.random_smooth(45, 67, 2, seed=5, model="B", wall_y=True),
+    "ragged68x45_N4_B_wally": lambda: W.random_smooth(68, 45, 4, seed=15, model="B", wall_y=True),
     "ragged130x33_N8_B_wallx": lambda: W.random_smooth(130, 33, 8, seed=6, model="B", wall_x=True),
     "ragged200x71_N6_A3": lambda: W.random_smooth(200, 71, 6, seed=7, model="A", model_a_n=3.0),
     "tiny5x7_N3_B": lambda: W.random_smooth(5, 7, 3, seed=8, model="B", n_disks=1),
