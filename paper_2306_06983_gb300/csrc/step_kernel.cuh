@@ -230,15 +230,16 @@ __device__ __forceinline__ void stage_flow_rows(const StepParams &P, int y, int 
     }
 }
 
-// Window columns lane l reads f_i (or g_i) at for a node row whose links
-// with c_iy = +1 (bl) or c_iy = -1 (bh) are bounced back at a y wall.
+// Window columns a node at window column b reads f_i (or g_i) at, for a
+// node row whose links with c_iy = +1 (bl) or c_iy = -1 (bh) are bounced
+// back at a y wall.
 struct WinCols {
     int b, c5, c6, c7, c8;   // c_0..c_4 follow from b: b, b - 1, b, b + 1, b
 };
-__device__ __forceinline__ WinCols win_cols(int lane, bool bl, bool bh)
+__device__ __forceinline__ WinCols win_cols(int b, bool bl, bool bh)
 {
     WinCols w;
-    w.b = 2 + lane;
+    w.b = b;
     w.c5 = bl ? w.b : w.b - 1;
     w.c6 = bl ? w.b : w.b + 1;
     w.c7 = bh ? w.b : w.b + 1;
@@ -368,6 +369,132 @@ __device__ __forceinline__ void sum_pulled16(const float *s_F, int WF, int col, 
             const unsigned h = ((par >> i) & 1u) ? (wd >> 16) : (wd & 0xffffu);
             f[i] = __fmaf_rn(w_of(i), own, Store16<ST>::dec(h));
         }
+        float s = f[0], e = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float t = s + f[i];
+            if (OWN) e += f[i] - (t - s);
+            s = t;
+        }
+        ph[p] = s;
+        if (OWN) {
+            plo[p] = e;
+            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        }
+    }
+}
+
+// Row windows of the 16-bit form (nx a multiple of 8, no wall across x).
+// Deviation planes: a window of kWin16 values (5 pieces of 8) starting at
+// the 8-aligned column ws at or left of the warp's first source column, so
+// lane l finds the value pulled along c_i at window column l + o16 - c_ix
+// (o16 = the warp's first node column - ws, 2 or 6).  FP32 planes read at the
+// node's own column (rest population, own phi) and the source pressure use
+// the kWin windows of the FP32 form.  Deviation pieces are copied by lanes
+// 0..29 (h = phase parity, group g, piece c), FP32 pieces by lanes 0..26.
+constexpr int kWin16 = 40;
+
+__device__ __forceinline__ void cp_async16_raw(void *dst_smem, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ unsigned wrap_col(int c, int nx)
+{
+    if (c < 0 || c >= nx) c = ((c % nx) + nx) % nx;
+    return (unsigned)c;
+}
+
+// Copies of what node row y (ring row, image row under a y wall) pulls:
+// the deviation windows s_Dw [8 NS][kWin16] and the rest-population and
+// own-phi windows s_Ow [2 NS][kWin] (rest populations first).
+template <int NS>
+__device__ __forceinline__ void stage_pull_rows16(const StepParams &P, int y, int lane, int ws, int xo,
+                                                  unsigned short *s_Dw, float *s_Ow)
+{
+    const unsigned pl = P.plane;
+    if (lane < 30) {
+        const int h = lane / 15, g = (lane % 15) / 5, c = lane % 5;
+        int ge;
+        unsigned row;
+        group_source(P, y, g, ge, row);
+        const unsigned short *base = (const unsigned short *)P.fin + (row + wrap_col(ws + 8 * c, P.nx));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (g == 0 && k == 0) continue;   // the rest population is FP32
+            const unsigned off = (unsigned)(group_dir(ge, k) - 1) * pl;
+            unsigned short *dst = s_Dw + (group_dir(g, k) - 1) * kWin16 + 8 * c;
+#pragma unroll
+            for (int m = 0; m < (NS + 1) / 2; ++m) {
+                const int p = h + 2 * m;
+                if (p < NS) cp_async16_raw(dst + 8 * p * kWin16, base + (size_t)p * 8 * pl + off);
+            }
+        }
+    }
+    if (lane < 27) {
+        const int g9 = lane / 9, c9 = lane % 9;
+        const unsigned own = (unsigned)y * (unsigned)P.nx + wrap_col(xo + 4 * c9, P.nx);
+#pragma unroll
+        for (int m = 0; m < (2 * NS + 2) / 3; ++m) {
+            const int q = g9 + 3 * m;
+            if (q < 2 * NS) {
+                const float *src = q < NS ? P.f0in + (size_t)q * pl : P.phi_prev + (size_t)(q - NS) * pl;
+                cp_async16(s_Ow + q * kWin + 4 * c9, src + own);
+            }
+        }
+    }
+}
+
+// Copies of what node row y (an own row) reads for its flow populations:
+// the deviation windows s_Gw [8][kWin16] and the pressure of the rows
+// y - 1, y, y + 1 at the source columns s_Pw [3][kWin] (the own row for a
+// link bounced at a y wall).
+__device__ __forceinline__ void stage_flow_rows16(const StepParams &P, int y, int lane, int ws, int xo,
+                                                  unsigned short *s_Gw, float *s_Pw)
+{
+    if (lane < 15) {
+        const int g = lane / 5, c = lane % 5;
+        int ge;
+        unsigned row;
+        group_source(P, y, g, ge, row);
+        const unsigned short *base = (const unsigned short *)P.gin + (row + wrap_col(ws + 8 * c, P.nx));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (g == 0 && k == 0) continue;   // g_0 is not stored
+            cp_async16_raw(s_Gw + (group_dir(g, k) - 1) * kWin16 + 8 * c,
+                           base + (unsigned)(group_dir(ge, k) - 1) * P.plane);
+        }
+    }
+    if (lane < 27) {
+        const int r9 = lane / 9, c9 = lane % 9;
+        int ys = y - 1 + r9;   // sources with c_iy = +1 sit on row y - 1 (slot 0)
+        if (ys < 0 || ys >= P.ny) ys = P.wall_y ? y : (ys < 0 ? ys + P.ny : ys - P.ny);
+        cp_async16(s_Pw + r9 * kWin + 4 * c9, P.pin + ((unsigned)ys * (unsigned)P.nx + wrap_col(xo + 4 * c9, P.nx)));
+    }
+}
+
+// sum_pulled16 from the warp's windows: f_i = w_i phi_own + dev_i.
+template <int NS, int ST, bool OWN>
+__device__ __forceinline__ void sum_pulled16_win(const unsigned short *s_Dw, const float *s_Ow, int lane,
+                                                 const WinCols &c, float (&ph)[NS], float (&plo)[NS],
+                                                 float (&jx)[NS], float (&jy)[NS])
+{
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+        const float own = s_Ow[(NS + p) * kWin + 2 + lane];
+        const unsigned short *d = s_Dw + 8 * p * kWin16;
+        float f[9];
+        f[0] = s_Ow[p * kWin + 2 + lane];
+        f[1] = __fmaf_rn(w_of(1), own, Store16<ST>::dec(d[c.b - 1]));
+        f[2] = __fmaf_rn(w_of(2), own, Store16<ST>::dec(d[kWin16 + c.b]));
+        f[3] = __fmaf_rn(w_of(3), own, Store16<ST>::dec(d[2 * kWin16 + c.b + 1]));
+        f[4] = __fmaf_rn(w_of(4), own, Store16<ST>::dec(d[3 * kWin16 + c.b]));
+        f[5] = __fmaf_rn(w_of(5), own, Store16<ST>::dec(d[4 * kWin16 + c.c5]));
+        f[6] = __fmaf_rn(w_of(6), own, Store16<ST>::dec(d[5 * kWin16 + c.c6]));
+        f[7] = __fmaf_rn(w_of(7), own, Store16<ST>::dec(d[6 * kWin16 + c.c7]));
+        f[8] = __fmaf_rn(w_of(8), own, Store16<ST>::dec(d[7 * kWin16 + c.c8]));
         float s = f[0], e = 0.f;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -525,15 +652,16 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
 // One tile of the fused step: the strip of columns [x0, x0 + T - 4) marching
 // rows [y0, y0 + TY) of the simulation described by P.  smem is the dynamic
 // shared memory of the block (step_smem_bytes gives its size).  VEC: the
-// pulled populations are staged as row windows (FP32 storage, nx a multiple
-// of 4, 16-byte aligned planes, no wall across x); otherwise every ring
-// thread copies the nine values its node pulls, 4 bytes at a time.
+// pulled populations are staged as row windows (nx a multiple of 4, of 8
+// with 16-bit storage, 16-byte aligned planes, no wall across x);
+// otherwise every ring thread copies the values its node pulls, 4 bytes at
+// a time.
 template <int NS, int MODEL, int T, int ST, bool VEC = false>
 __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, const int y0, const int TY,
                                           float *smem)
 {
-    static_assert(!VEC || ST == 0, "row windows stage FP32 populations");
     constexpr int N = NS + 1;
+    constexpr bool V32 = VEC && ST == 0, V16 = VEC && ST != 0;
     // Thread t owns ring column t, lattice column x0 - 2 + t: every thread
     // pulls one phase field in stage A, the inner T - 2 compute m_phi in
     // stage B and the inner T - 4 (the strip) complete their node in stage
@@ -546,6 +674,13 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                                              // ([10NS][T] with 16-bit storage, see prefetch_pull16;
                                              // VEC: [T/32][9NS][kWin] row windows)
     float *s_G = s_F + (T / 32) * 9 * NS * kWin;   // VEC: [2][T/32][8][kWin] g windows of two rows
+    // VEC with 16-bit storage: [T/32][8NS][kWin16] deviation and [T/32][2NS][kWin]
+    // rest-population / own-phi windows, then per row parity [T/32][8][kWin16] g
+    // deviations and [T/32][3][kWin] pressure rows
+    unsigned short *s_D16 = (unsigned short *)s_F;
+    float *s_O16 = (float *)(s_D16 + (T / 32) * 8 * NS * kWin16);
+    unsigned short *s_G16 = (unsigned short *)(s_O16 + (T / 32) * 2 * NS * kWin);
+    float *s_P16 = (float *)(s_G16 + 2 * (T / 32) * 8 * kWin16);
 
     const int t = threadIdx.x;
     const int We = min(W, P.nx - x0), TYe = min(TY, P.ny - y0);
@@ -561,16 +696,21 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     unsigned par_next = 0, par_cur = 0;   // halves of the staged 16-bit words
     // VEC: this lane's window piece and direction group, the (wrapped)
     // lattice column of that piece, and the warp's windows.
-    const int lane = t & 31, wc = lane % 9, wg = lane / 9;
-    const bool copier = VEC && lane < 27 && 32 * (t >> 5) < We + 4;
+    const int lane = t & 31, wc = lane % 9, wg = lane / 9, warp = t >> 5;
+    const bool copier = V32 ? (lane < 27 && 32 * warp < We + 4) : (V16 && 32 * warp < We + 4);
     unsigned wcol = 0;
-    if constexpr (VEC) {
-        int c = x0 - 4 + 32 * (t >> 5) + 4 * wc;
+    if constexpr (V32) {
+        int c = x0 - 4 + 32 * warp + 4 * wc;
         if (c < 0 || c >= nx) c = ((c % nx) + nx) % nx;   // periodic x: a piece never straddles the edge
         wcol = (unsigned)c;
     }
-    float *s_Fw = s_F + (t >> 5) * 9 * NS * kWin;
-    float *s_Gw = s_G + (t >> 5) * 8 * kWin;   // + (row & 1) * (T / 32) * 8 * kWin
+    float *s_Fw = s_F + warp * 9 * NS * kWin;
+    float *s_Gw = s_G + warp * 8 * kWin;   // + (row & 1) * (T / 32) * 8 * kWin
+    // 16-bit windows of this warp: first column of the deviation windows (ws),
+    // of the FP32 windows (xo), and the window column of lane 0's node (o16)
+    const int xo = x0 - 4 + 32 * warp, ws = ((x0 - 3 + 32 * warp) >> 3) * 8, o16 = x0 - 2 + 32 * warp - ws;
+    unsigned short *s_Dw = s_D16 + warp * 8 * NS * kWin16;
+    float *s_Ow = s_O16 + warp * 2 * NS * kWin;
     // The pulled populations of row r+1 are copied into shared memory
     // (cp.async) while rows r..r-2 are computed.  Without VEC each thread
     // only reads the slots it filled itself; with VEC the warp barrier after
@@ -578,8 +718,10 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     {
         bool yflip;
         const int ya = map_axis(y0 - 2, P.ny, P.wall_y, yflip);
-        if constexpr (VEC) {
+        if constexpr (V32) {
             if (copier) stage_pull_rows<NS>(P, ya, wg, wc, wcol, s_Fw);
+        } else if constexpr (V16) {
+            if (copier) stage_pull_rows16<NS>(P, ya, lane, ws, xo, s_Dw, s_Ow);
         } else if (in_ring) {
             if constexpr (ST == 0) prefetch_pull<NS>(P, xc, ya, s_F, T, t);
             else par_next = prefetch_pull16<NS>(P, xc, ya, s_F, T, t);
@@ -603,8 +745,12 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     float ub_x = 0.f, ub_y = 0.f;                       // u(t-1) for stage B of this iteration
     float ub_s = 1.f;                                   // its sign: -1 on a no-slip ghost node
 
+    // ring slots of row ra (5-row phi ring, 3-row rings), advanced each iteration
+    int a5 = slot5(y0 - 2), a3 = slot3(y0 - 2);
     for (int it = 0; it < TYe + 4; ++it) {
         const int ra = y0 - 2 + it;
+        const int a5m1 = a5 == 0 ? 4 : a5 - 1, a5m2 = a5 >= 2 ? a5 - 2 : a5 + 3, a5m3 = a5 >= 3 ? a5 - 3 : a5 + 2;
+        const int a3m1 = a3 == 0 ? 2 : a3 - 1, a3m2 = a3 >= 2 ? a3 - 2 : a3 + 1;
         // stage-C inputs of row ra - 2, requested before stages A and B
         // (loaded raw; anything computed from them waits until stage C, so
         // that the loads overlap stages A and B)
@@ -657,18 +803,19 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             if constexpr (VEC) {
                 bool yflip;
                 const int yi = map_axis(ra, P.ny, P.wall_y, yflip);
-                const WinCols wcl = win_cols(lane, P.wall_y && yi == 0, P.wall_y && yi == P.ny - 1);
-                sum_pulled_win<NS, true>(s_Fw, wcl, ph, plo, jx, jy);
+                const bool bl = P.wall_y && yi == 0, bh = P.wall_y && yi == P.ny - 1;
+                if constexpr (V32) sum_pulled_win<NS, true>(s_Fw, win_cols(2 + lane, bl, bh), ph, plo, jx, jy);
+                else sum_pulled16_win<NS, ST, true>(s_Dw, s_Ow, lane, win_cols(lane + o16, bl, bh), ph, plo, jx, jy);
             } else if constexpr (ST == 0) {
                 sum_pulled<NS, true>(s_F, T, t, ph, plo, jx, jy);
             } else {
                 sum_pulled16<NS, ST, true>(s_F, T, t, par_cur, ph, plo, jx, jy);
             }
-            const int s5 = slot5(ra);
+            const int s5 = a5;
 #pragma unroll
             for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
             if (own && ra >= y0 && ra < y0 + TYe) {
-                const int s3 = slot3(ra);
+                const int s3 = a3;
 #pragma unroll
                 for (int p = 0; p < NS; ++p) {
                     s_j[(s3 * 3 * NS + 3 * p) * T + t] = jx[p];
@@ -688,12 +835,20 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             if (copier) {
                 if (it + 1 < TYe + 4) {
                     bool yflip;
-                    stage_pull_rows<NS>(P, map_axis(ra + 1, P.ny, P.wall_y, yflip), wg, wc, wcol, s_Fw);
+                    const int yn = map_axis(ra + 1, P.ny, P.wall_y, yflip);
+                    if constexpr (V32) stage_pull_rows<NS>(P, yn, wg, wc, wcol, s_Fw);
+                    else stage_pull_rows16<NS>(P, yn, lane, ws, xo, s_Dw, s_Ow);
                 }
                 // g of the row stage C completes next iteration
                 const int yg = ra - 1;
-                if (it >= 3 && yg < y0 + TYe)
-                    stage_flow_rows(P, yg, wg, wc, wcol, s_Gw + (yg & 1) * (T / 32) * 8 * kWin);
+                if (it >= 3 && yg < y0 + TYe) {
+                    if constexpr (V32) {
+                        stage_flow_rows(P, yg, wg, wc, wcol, s_Gw + (yg & 1) * (T / 32) * 8 * kWin);
+                    } else {
+                        const int b = (yg & 1) * (T / 32) + warp;
+                        stage_flow_rows16(P, yg, lane, ws, xo, s_G16 + b * 8 * kWin16, s_P16 + b * 3 * kWin);
+                    }
+                }
             }
         }
         cp_async_commit();
@@ -701,16 +856,16 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
         // ---------------------------------------------------- stage B
         if (it >= 2) {
             const int rb = ra - 1;
-            const int s3 = slot3(rb);
+            const int s3 = a3m1;
             if (in_flux) {
                 float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
                 if constexpr (ST == 0) {
                     float lap[N];
-                    window_grad_lap<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy, lap);
+                    window_grad_lap<NS>(s_phi, T, a5m2, a5m1, a5, t, ph, gx, gy, lap);
 #pragma unroll
                     for (int p = 0; p < NS; ++p) { PHn[p] = ph[p]; GXn[p] = gx[p]; GYn[p] = gy[p]; LPn[p] = lap[p]; }
                 } else {
-                    window_grad<NS>(s_phi, T, slot5(rb - 1), slot5(rb), slot5(rb + 1), t, ph, gx, gy);
+                    window_grad<NS>(s_phi, T, a5m2, a5m1, a5, t, ph, gx, gy);
                 }
                 source_terms<NS, MODEL>(P, ph, gx, gy, Rx, Ry);
                 mass_flux<NS>(P, gx, gy, Rx, Ry, mx, my);
@@ -727,7 +882,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
         // ---------------------------------------------------- stage C
         if (do_c) {
             const int y = ra - 2;
-            const int sm = slot5(y - 1), s0 = slot5(y), sp = slot5(y + 1);
+            const int sm = a5m3, s0 = a5m2, sp = a5m1;
             float ph[N], gx[N], gy[N], lap[N];
             if constexpr (ST == 0) {
                 float sph = 0.f, sgx = 0.f, sgy = 0.f, sl = 0.f;
@@ -789,9 +944,9 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             // F_c = -div(m_phi u - u m_phi)/2 with the previous velocity:
             // with w = m_x u_y - u_x m_y, F_c = (d_y w / 2, -d_x w / 2).
             {
-                const float *wm = s_w + slot3(y - 1) * T + t;
-                const float *w0 = s_w + slot3(y) * T + t;
-                const float *wp = s_w + slot3(y + 1) * T + t;
+                const float *wm = s_w + a3 * T + t;
+                const float *w0 = s_w + a3m2 * T + t;
+                const float *wp = s_w + a3m1 * T + t;
                 const float wsw = wm[-1], ws = wm[0], wse = wm[1];
                 const float ww = w0[-1], we = w0[1];
                 const float wnw = wp[-1], wn = wp[0], wne = wp[1];
@@ -802,9 +957,32 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             }
 
             // macroscopic velocity (Eq. (25b)) and mass flux (Eq. (13))
-            if constexpr (VEC) {
+            if constexpr (V16) {
+                const int b = (y & 1) * (T / 32) + warp;
+                const unsigned short *gd = s_G16 + b * 8 * kWin16;
+                const float *pw = s_P16 + b * 3 * kWin;   // rows y - 1, y, y + 1
+                const bool bl = P.wall_y && y == 0, bh = P.wall_y && y == P.ny - 1;
+                const WinCols wd = win_cols(lane + o16, bl, bh), wp = win_cols(2 + lane, bl, bh);
+                gq[1] = gd[wd.b - 1];
+                gq[2] = gd[kWin16 + wd.b];
+                gq[3] = gd[2 * kWin16 + wd.b + 1];
+                gq[4] = gd[3 * kWin16 + wd.b];
+                gq[5] = gd[4 * kWin16 + wd.c5];
+                gq[6] = gd[5 * kWin16 + wd.c6];
+                gq[7] = gd[6 * kWin16 + wd.c7];
+                gq[8] = gd[7 * kWin16 + wd.c8];
+                gps[1] = pw[kWin + wp.b - 1];
+                gps[2] = pw[(bl ? kWin : 0) + wp.b];
+                gps[3] = pw[kWin + wp.b + 1];
+                gps[4] = pw[(bh ? kWin : 2 * kWin) + wp.b];
+                gps[5] = pw[(bl ? kWin : 0) + wp.c5];
+                gps[6] = pw[(bl ? kWin : 0) + wp.c6];
+                gps[7] = pw[(bh ? kWin : 2 * kWin) + wp.c7];
+                gps[8] = pw[(bh ? kWin : 2 * kWin) + wp.c8];
+            }
+            if constexpr (V32) {
                 const float *gw = s_Gw + (y & 1) * (T / 32) * 8 * kWin;
-                const WinCols wcl = win_cols(lane, P.wall_y && y == 0, P.wall_y && y == P.ny - 1);
+                const WinCols wcl = win_cols(2 + lane, P.wall_y && y == 0, P.wall_y && y == P.ny - 1);
                 g[1] = gw[wcl.b - 1];
                 g[2] = gw[kWin + wcl.b];
                 g[3] = gw[2 * kWin + wcl.b + 1];
@@ -843,7 +1021,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             const float Pr = 0.6f * (sg + 0.5f * ugr - (2.f / 3.f) * mu_t + (1.f / 3.f) * (mu_t - mu_prev));
 
             // phase-field collisions, Eqs. (18),(19) in moment space
-            const int s3 = slot3(y);
+            const int s3 = a3m2;
             // links of this node that end in a wall: their population comes
             // back to this node (half-way bounce-back)
             const bool bxl = P.wall_x && xg == 0, bxh = P.wall_x && xg == nx - 1;
@@ -984,6 +1162,8 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
         ub_x = ua_x;
         ub_y = ua_y;
         ub_s = ua_s;
+        a5 = a5 == 4 ? 0 : a5 + 1;
+        a3 = a3 == 2 ? 0 : a3 + 1;
     }
 }
 
@@ -1013,11 +1193,14 @@ __global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
 
 // Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
 // the staging rows (9 slots per phase, 10 with 16-bit storage; VEC: the
-// warps' f windows and two rows of g windows).
+// warps' pull windows and two rows of flow windows).
 template <int NS, int T, int ST, bool VEC = false>
 constexpr size_t step_smem_bytes()
 {
-    if (VEC) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
+    if (VEC && ST == 0) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
+    if (VEC)   // 16-bit deviation windows (2 bytes a value) and FP32 windows
+        return sizeof(float) * (size_t)T * (14 * NS + 3) +
+               (size_t)(T / 32) * (2 * kWin16 * (8 * NS + 16) + sizeof(float) * kWin * (2 * NS + 6));
     return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
 }
 
@@ -1069,8 +1252,8 @@ cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStr
     return cudaGetLastError();
 }
 
-// Row windows need FP32 storage, nx a multiple of 4 (rows and planes start
-// on 16-byte boundaries), 16-byte aligned population arrays and no wall
+// Row windows need nx a multiple of 4 (of 8 with 16-bit storage: rows and
+// planes start on 16-byte boundaries), 16-byte aligned arrays and no wall
 // across x (a wall bounces single columns back, which a window cannot
 // express); they are used unless their larger shared memory would leave
 // fewer blocks resident.
@@ -1083,9 +1266,12 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     int plain = 0;
     if ((e = variant_slots<NS, MODEL, T, ST, false>(dev, &plain)) != cudaSuccess) return e;
-    if constexpr (ST == 0) {
-        const bool vec = !p.wall_x && p.nx % 4 == 0 &&
-                         ((reinterpret_cast<uintptr_t>(p.fin) | reinterpret_cast<uintptr_t>(p.gin)) & 15) == 0;
+    {
+        uintptr_t a = reinterpret_cast<uintptr_t>(p.fin) | reinterpret_cast<uintptr_t>(p.gin);
+        if (ST != 0)
+            a |= reinterpret_cast<uintptr_t>(p.f0in) | reinterpret_cast<uintptr_t>(p.phi_prev) |
+                 reinterpret_cast<uintptr_t>(p.pin);
+        const bool vec = !p.wall_x && p.nx % (ST == 0 ? 4 : 8) == 0 && (a & 15) == 0;
         int win = 0;
         if (vec && (e = variant_slots<NS, MODEL, T, ST, true>(dev, &win)) != cudaSuccess) return e;
         if (vec && win >= plain) return launch_step_variant<NS, MODEL, T, ST, true>(p, ty, win, st);

@@ -78,6 +78,7 @@ CASES = {
     "walls68x46_N4_A": lambda: W.random_smooth(68, 46, 4, seed=4, model="A", model_a_n=1.5,
                                                wall_x=True, wall_y=True),
     "wally46x67_N2_B": lambda: W.random_smooth(46, 67, 2, seed=5, model="B", wall_y=True),
+    "wally48x67_N2_B": lambda: W.random_smooth(48, 67, 2, seed=16, model="B", wall_y=True),
     "wallx130x33_N8_B": lambda: W.random_smooth(130, 33, 8, seed=6, model="B", wall_x=True),
     "ragged200x71_N6_A3": lambda: W.random_smooth(200, 71, 6, seed=7, model="A", model_a_n=3.0),
     "tiny8x8_N7_A": lambda: W.random_smooth(8, 8, 7, seed=9, model="A", n_disks=3),
