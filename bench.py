@@ -547,7 +547,8 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=None, metavar=("TX", "TY"))
     ap.add_argument("--lattice", type=int, nargs=2, default=None, metavar=("NX", "NY"),
                     help="profiling aid: a disk suspension of this size instead of 2048x2048")
-    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-steps", type=int, default=500,
+                    help="oracle steps of the CPU baseline (about 10 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the 16-bit storage and ensemble forms measured beside the headline")

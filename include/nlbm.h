@@ -170,7 +170,7 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s);
 /* Tile of the fused step kernel: tx threads per block (64, 128 or 256; one
  * thread per column, each block updating a strip of tx - 4 columns) marching
  * down ty rows (>= 1), or ty = 0 (the default) to let the library cut every
- * strip into equal row chunks (at least 16 rows) so that the grid is one
+ * strip into equal row chunks (at least 2 rows) so that the grid is one
  * wave of resident blocks.  EINVAL outside those values.  Takes effect on
  * the next nlbm_step(). */
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
@@ -294,7 +294,8 @@ typedef struct nlbm_adjoint nlbm_adjoint;
 
 /* Device workspace bytes for nsteps >= 1 steps with a checkpoint every
  * checkpoint_every >= 1 steps: the simulation, ceil(nsteps / every)
- * checkpoints and `every` segment states of 10(N-1)+12 floats a node, the
+ * checkpoints and every + 1 segment states of 10(N-1)+12 floats a node,
+ * `every` tapes of the segment's steps (8(N-1)+13 floats a node), the
  * adjoint fields.  Host only. */
 nlbm_status nlbm_adjoint_workspace_bytes(const nlbm_params *p, int32_t nsteps, int32_t checkpoint_every,
                                          size_t *bytes);

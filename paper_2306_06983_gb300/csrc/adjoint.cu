@@ -671,12 +671,14 @@ int blocks_for(unsigned n)
 }
 
 template <int NS>
-cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st)
+cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped, cudaStream_t st)
 {
     const int nb = blocks_for(P.plane);
-    tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
-    tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
-    tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+    if (!taped) {
+        tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+        tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+        tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+    }
     rev_collide_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
     rev_source_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
     rev_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, A);
@@ -700,11 +702,12 @@ __global__ void add_planes_kernel(const float *__restrict__ a, const float *__re
 
 }  // namespace
 
-cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st)
+cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped,
+                                cudaStream_t st)
 {
     switch (ns) {
 #define NLBM_CASE(K) \
-    case K: return reverse_step_ns<K>(P, T, A, st);
+    case K: return reverse_step_ns<K>(P, T, A, taped, st);
         NLBM_CASE(1) NLBM_CASE(2) NLBM_CASE(3) NLBM_CASE(4) NLBM_CASE(5) NLBM_CASE(6) NLBM_CASE(7)
 #undef NLBM_CASE
     default: return cudaErrorInvalidValue;

@@ -46,8 +46,11 @@ struct AdjFields {
 
 // Tape and reverse of one step whose input state P describes (P.fin, P.gin,
 // P.phi_prev, P.uin, P.mphi); adds this step's parameter-gradient terms to
-// A.gacc node by node.
-cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, cudaStream_t st);
+// A.gacc node by node.  taped: T already holds the step's intermediate
+// fields (written by the taping forward kernel), so only the four reverse
+// passes run.
+cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped,
+                                cudaStream_t st);
 // acc[c] = sum over nodes of gacc[c][node], c < K, in a fixed order (FP64).
 cudaError_t launch_grad_reduce(const double *gacc, int K, unsigned plane, double *partials, double *acc,
                                cudaStream_t st);

@@ -944,8 +944,9 @@ struct nlbm_adjoint {
     cudaStream_t stream;
     char *ws;
     float *ckpt;               // [nckpt][state]
-    float *seg;                // [every][state]
-    AdjTape T;
+    float *seg;                // [every + 1][state]
+    float *tapes;              // [every][tape] the rebuilt segment's tapes
+    AdjTape T;                 // the tape of nlbm_adjoint_reverse_step
     float *seed[2];            // two sets of step-output adjoints
     AdjFields A;               // intermediates (the seed pointers are set per step)
     double *partials, *acc;    // [kAdjRedBlocks][NP+1], [NP+1]
@@ -978,7 +979,7 @@ AdjCounts adj_counts(int ns)
 }
 
 struct AdjLayout {
-    size_t sim, ckpt, seg, fields, partials, acc, total;
+    size_t sim, ckpt, seg, tapes, fields, partials, acc, total;
 };
 
 nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L, char *err)
@@ -1003,7 +1004,11 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
     };
     L->sim = take(make_layout(ns, plane, false).total);
     L->ckpt = take(sizeof(float) * adj_state_floats(ns, plane) * nckpt);
-    L->seg = take(sizeof(float) * adj_state_floats(ns, plane) * (size_t)(every < nsteps ? every : nsteps));
+    // a segment's states and one spare (the output of its last step), and
+    // the tape of each of its steps
+    const size_t seglen = (size_t)(every < nsteps ? every : nsteps);
+    L->seg = take(sizeof(float) * adj_state_floats(ns, plane) * (seglen + 1));
+    L->tapes = take(sizeof(float) * plane * (size_t)c.tape * seglen);
     // the FP64 per-node sums come first (8-byte alignment)
     L->fields = take(sizeof(float) * plane * (size_t)(c.contrib + c.tape + 2 * c.seedset + c.inter + 2 * ns + 1));
     L->partials = take(sizeof(double) * kAdjRedBlocks * c.contrib);
@@ -1084,12 +1089,31 @@ AdjFields adj_fields(const nlbm_adjoint *a, float *so, float *si)
     return A;
 }
 
+// Tape k of the rebuilt segment (the field order of launch_step_tape_b_f32).
+AdjTape adj_tape(const nlbm_adjoint *a, int k)
+{
+    const size_t pl = a->plane;
+    const int ns = a->ns;
+    float *b = a->tapes + pl * (size_t)adj_counts(ns).tape * k;
+    AdjTape T;
+    T.phi = b;
+    T.j = b + pl * ns;
+    T.g = b + pl * 3 * ns;
+    T.grad = b + pl * (3 * ns + 8);
+    T.lap = b + pl * (5 * ns + 8);
+    T.R = b + pl * (6 * ns + 8);
+    T.mphi = b + pl * (8 * ns + 8);
+    T.w = b + pl * (8 * ns + 10);
+    T.F = b + pl * (8 * ns + 11);
+    return T;
+}
+
 // Kernel launches of one reverse sweep (counted, not queried).
 int64_t adj_sweep_launches(const nlbm_adjoint *a)
 {
-    // fold + per step: 7 reverse kernels; recompute: one step kernel per
-    // rebuilt state; the phi0 sum and the two-kernel reduction
-    return 1 + 7 * (int64_t)a->nsteps + (a->nsteps - a->nckpt) + 1 + 2;
+    // fold + per step: one taping step kernel while the segment is rebuilt
+    // and 4 reverse kernels; the phi0 sum and the two-kernel reduction
+    return 1 + 5 * (int64_t)a->nsteps + 1 + 2;
 }
 
 // The reverse sweep, asynchronous and capturable: seeds from seed_buf,
@@ -1109,11 +1133,13 @@ cudaError_t adj_backward_body(nlbm_adjoint *a)
     for (int k = a->nckpt - 1; k >= 0; --k) {
         const int t0 = k * a->every;
         const int len = (k + 1) * a->every <= a->nsteps ? a->every : a->nsteps - t0;
-        // rebuild the segment's input states S_t0 .. S_t0+len-1 in place
+        // rebuild the segment's input states S_t0 .. S_t0+len-1 in place and,
+        // with the same launches, the tape of each of its steps (the last
+        // step's output state goes to the spare slot)
         if ((e = cudaMemcpyAsync(a->seg, a->ckpt + a->state_floats * k, sizeof(float) * a->state_floats,
                                  cudaMemcpyDeviceToDevice, a->stream)) != cudaSuccess)
             return e;
-        for (int s = 1; s < len; ++s) {
+        for (int s = 1; s <= len; ++s) {
             const float *in = a->seg + a->state_floats * (s - 1);
             float *out = a->seg + a->state_floats * s;
             StepParams kp = adj_params_from_state(a, in);
@@ -1126,12 +1152,13 @@ cudaError_t adj_backward_body(nlbm_adjoint *a)
             if ((e = cudaMemcpyAsync(kp.mphi, in + (kp.mphi - out), pb * 2, cudaMemcpyDeviceToDevice, a->stream)) !=
                 cudaSuccess)
                 return e;
-            if ((e = launch_step(a->sim, kp)) != cudaSuccess) return e;
+            kp.tape = a->tapes + pl * (size_t)c.tape * (s - 1);
+            if ((e = launch_step_tape_b_f32(ns, kp, a->stream)) != cudaSuccess) return e;
         }
         for (int s = len - 1; s >= 0; --s) {
             const StepParams kp = adj_params_from_state(a, a->seg + a->state_floats * s);
             const AdjFields A = adj_fields(a, a->seed[cur], a->seed[cur ^ 1]);
-            if ((e = launch_reverse_step(ns, kp, a->T, A, a->stream)) != cudaSuccess) return e;
+            if ((e = launch_reverse_step(ns, kp, adj_tape(a, s), A, true, a->stream)) != cudaSuccess) return e;
             cur ^= 1;
         }
     }
@@ -1196,6 +1223,7 @@ nlbm_status nlbm_adjoint_create(const nlbm_params *p, int32_t nsteps, int32_t ch
     a->ws = ws;
     a->ckpt = (float *)(ws + L.ckpt);
     a->seg = (float *)(ws + L.seg);
+    a->tapes = (float *)(ws + L.tapes);
     const AdjCounts c = adj_counts(a->ns);
     const size_t pl = a->plane;
     float *f = (float *)(ws + L.fields);
@@ -1322,7 +1350,7 @@ nlbm_status nlbm_adjoint_reverse_step(nlbm_adjoint *a, const float *dev_state, c
         (e = cudaMemsetAsync(a->A.gacc, 0, pb * c.contrib, a->stream)) != cudaSuccess)
         return adj_fail(a, e, "seed");
     const StepParams kp = adj_params_from_state(a, dev_state);
-    if ((e = launch_reverse_step(ns, kp, a->T, adj_fields(a, a->seed[0], a->seed[1]), a->stream)) != cudaSuccess ||
+    if ((e = launch_reverse_step(ns, kp, a->T, adj_fields(a, a->seed[0], a->seed[1]), false, a->stream)) != cudaSuccess ||
         (e = launch_grad_reduce(a->A.gacc, np + 1, (unsigned)pl, a->partials, a->acc, a->stream)) != cudaSuccess)
         return adj_fail(a, e, "reverse step");
     a->sim->launches += 9;

@@ -64,6 +64,7 @@ struct StepParams {
     float *pout;               // [plane] or nullptr
     int model;                 // 0 Model A, 1 Model B (read by the ensemble kernel)
     int row_window;            // ensemble kernel: stage pulls as row windows (see step_tile)
+    float *tape;               // adjoint recompute: the step's intermediate fields (launch_step_tape)
 };
 
 // One work item of the ensemble kernel: the strip of simulation `sim` that
@@ -81,6 +82,12 @@ cudaError_t launch_step_a_bf16(int ns, const StepParams &p, int tx, int ty, cuda
 cudaError_t launch_step_b_bf16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 cudaError_t launch_step_a_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 cudaError_t launch_step_b_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
+
+// The FP32 Model B step (128-thread blocks) that also writes the step's
+// intermediate fields for the adjoint to p.tape, 8 (N-1) + 13 planes in the
+// order of AdjTape: phi [N-1], j [2(N-1)], pulled g [8], grad phi [2(N-1)],
+// lap phi [N-1], R [2(N-1)], m_phi [2], w [1], F [2] (step_b_f32_tape.cu).
+cudaError_t launch_step_tape_b_f32(int ns, const StepParams &p, cudaStream_t st);
 
 // Ensemble of independent simulations (batch.cu): one persistent launch
 // advances every simulation of the table one step; blocks take tiles from

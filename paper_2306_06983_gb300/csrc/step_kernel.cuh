@@ -656,12 +656,13 @@ __device__ __forceinline__ void mass_flux(const StepParams &P, const float (&gx)
 // with 16-bit storage, 16-byte aligned planes, no wall across x);
 // otherwise every ring thread copies the values its node pulls, 4 bytes at
 // a time.
-template <int NS, int MODEL, int T, int ST, bool VEC = false>
+template <int NS, int MODEL, int T, int ST, bool VEC = false, bool TAPE = false>
 __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, const int y0, const int TY,
                                           float *smem)
 {
     constexpr int N = NS + 1;
     constexpr bool V32 = VEC && ST == 0, V16 = VEC && ST != 0;
+    static_assert(!TAPE || ST == 0, "the adjoint tape is written by the FP32 form");
     // Thread t owns ring column t, lattice column x0 - 2 + t: every thread
     // pulls one phase field in stage A, the inner T - 2 compute m_phi in
     // stage B and the inner T - 4 (the strip) complete their node in stage
@@ -1145,6 +1146,29 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             P.mphi[node] = mphx;
             P.mphi[pl + node] = mphy;
             if (P.pout) P.pout[node] = Pr;
+            if constexpr (TAPE) {
+                // the intermediate fields of this step at this node, for the
+                // adjoint: phi, j, pulled g, grad phi, lap phi, R, m_phi, w, F
+                float *tp = P.tape + node;
+#pragma unroll
+                for (int p = 0; p < NS; ++p) {
+                    tp[(size_t)p * pl] = ph[p];
+                    tp[(size_t)(NS + 2 * p) * pl] = s_j[(s3 * 3 * NS + 3 * p) * T + t];
+                    tp[(size_t)(NS + 2 * p + 1) * pl] = s_j[(s3 * 3 * NS + 3 * p + 1) * T + t];
+                    tp[(size_t)(3 * NS + 8 + 2 * p) * pl] = gx[p];
+                    tp[(size_t)(3 * NS + 9 + 2 * p) * pl] = gy[p];
+                    tp[(size_t)(5 * NS + 8 + p) * pl] = lap[p];
+                    tp[(size_t)(6 * NS + 8 + 2 * p) * pl] = Rcx[p];
+                    tp[(size_t)(6 * NS + 9 + 2 * p) * pl] = Rcy[p];
+                }
+#pragma unroll
+                for (int i = 1; i < 9; ++i) tp[(size_t)(3 * NS + i - 1) * pl] = g[i];
+                tp[(size_t)(8 * NS + 8) * pl] = mphx;
+                tp[(size_t)(8 * NS + 9) * pl] = mphy;
+                tp[(size_t)(8 * NS + 10) * pl] = s_w[a3m2 * T + t];
+                tp[(size_t)(8 * NS + 11) * pl] = Fx;
+                tp[(size_t)(8 * NS + 12) * pl] = Fy;
+            }
         }
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -1170,7 +1194,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 // Grid: one block per (strip, row chunk), strips of T - 4 columns, strip
 // index fastest.  TY > 0: chunks of TY rows; TY = 0: chunk k of `chunks`
 // covers rows [k ny / chunks, (k + 1) ny / chunks).
-template <int NS, int MODEL, int T, int ST, bool VEC>
+template <int NS, int MODEL, int T, int ST, bool VEC, bool TAPE = false>
 // FP32: three blocks of 128 threads per SM, up to 170 registers a thread
 // (measured: the throughput is flat between 12 and 16 resident warps and
 // falls when the registers are squeezed to fit more).  16-bit storage: four.
@@ -1188,7 +1212,7 @@ __global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
         ty = (int)((long long)(k + 1) * P.ny / chunks) - y0;
     }
     if (ty <= 0 || y0 >= P.ny) return;
-    step_tile<NS, MODEL, T, ST, VEC>(P, s * (T - 4), y0, ty, smem);
+    step_tile<NS, MODEL, T, ST, VEC, TAPE>(P, s * (T - 4), y0, ty, smem);
 }
 
 // Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
@@ -1206,17 +1230,17 @@ constexpr size_t step_smem_bytes()
 
 // Resident blocks of one kernel variant on device dev (the dynamic
 // shared-memory limit, a per-device function attribute, is set on first use).
-template <int NS, int MODEL, int T, int ST, bool VEC>
+template <int NS, int MODEL, int T, int ST, bool VEC, bool TAPE = false>
 cudaError_t variant_slots(int dev, int *out)
 {
     constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
     static int slots[64] = {0};
     if (!slots[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST, VEC>,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST, VEC, TAPE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T, ST, VEC>, T, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<NS, MODEL, T, ST, VEC, TAPE>, T, smem);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -1226,7 +1250,7 @@ cudaError_t variant_slots(int dev, int *out)
     return cudaSuccess;
 }
 
-template <int NS, int MODEL, int T, int ST, bool VEC>
+template <int NS, int MODEL, int T, int ST, bool VEC, bool TAPE = false>
 cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStream_t st)
 {
     constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
@@ -1237,18 +1261,21 @@ cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStr
     } else {
         // Automatic march length: as many row chunks per strip as there are
         // resident-block slots per strip (one full wave), chunks of at least
-        // 16 rows.  Every chunk, of a narrow last strip too, gets the same
-        // rows: a block's time per row hardly depends on how many of its
-        // warps hold ring columns.
+        // 2 rows.  On a lattice too small to fill the GPU, short chunks put
+        // more SMs to work although each repeats the 4 + 2 pre-roll rows
+        // (measured: 256^2 N=5 at 2 rows 3,188 MLUPS, at 16 rows 1,675).
+        // Every chunk, of a narrow last strip too, gets the same rows: a
+        // block's time per row hardly depends on how many of its warps hold
+        // ring columns.
         chunks = nslots / strips;
-        const int maxc = p.ny / 16 > 1 ? p.ny / 16 : 1;
+        const int maxc = p.ny / 2 > 1 ? p.ny / 2 : 1;
         if (chunks > maxc) chunks = maxc;
         if (chunks < 1) chunks = 1;
         ty = 0;
     }
     const long long blocks = (long long)strips * chunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_kernel<NS, MODEL, T, ST, VEC><<<(unsigned)blocks, T, smem, st>>>(p, ty, chunks, strips);
+    step_kernel<NS, MODEL, T, ST, VEC, TAPE><<<(unsigned)blocks, T, smem, st>>>(p, ty, chunks, strips);
     return cudaGetLastError();
 }
 
@@ -1257,7 +1284,7 @@ cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStr
 // across x (a wall bounces single columns back, which a window cannot
 // express); they are used unless their larger shared memory would leave
 // fewer blocks resident.
-template <int NS, int MODEL, int T, int ST>
+template <int NS, int MODEL, int T, int ST, bool TAPE = false>
 cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
     int dev = 0;
@@ -1265,7 +1292,7 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     int plain = 0;
-    if ((e = variant_slots<NS, MODEL, T, ST, false>(dev, &plain)) != cudaSuccess) return e;
+    if ((e = variant_slots<NS, MODEL, T, ST, false, TAPE>(dev, &plain)) != cudaSuccess) return e;
     {
         uintptr_t a = reinterpret_cast<uintptr_t>(p.fin) | reinterpret_cast<uintptr_t>(p.gin);
         if (ST != 0)
@@ -1273,10 +1300,10 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
                  reinterpret_cast<uintptr_t>(p.pin);
         const bool vec = !p.wall_x && p.nx % (ST == 0 ? 4 : 8) == 0 && (a & 15) == 0;
         int win = 0;
-        if (vec && (e = variant_slots<NS, MODEL, T, ST, true>(dev, &win)) != cudaSuccess) return e;
-        if (vec && win >= plain) return launch_step_variant<NS, MODEL, T, ST, true>(p, ty, win, st);
+        if (vec && (e = variant_slots<NS, MODEL, T, ST, true, TAPE>(dev, &win)) != cudaSuccess) return e;
+        if (vec && win >= plain) return launch_step_variant<NS, MODEL, T, ST, true, TAPE>(p, ty, win, st);
     }
-    return launch_step_variant<NS, MODEL, T, ST, false>(p, ty, plain, st);
+    return launch_step_variant<NS, MODEL, T, ST, false, TAPE>(p, ty, plain, st);
 }
 
 template <int NS, int MODEL, int ST>
