@@ -212,6 +212,7 @@ StepParams step_params(const nlbm_sim *s, int a, int b)
     kp.phi_prev = s->phi(a);
     kp.phi = s->phi(b);
     kp.mphi = s->mphi();
+    kp.mphi_in = kp.mphi;
     kp.pin = s->P(a);
     kp.pout = s->P(b);
     return kp;
@@ -1066,6 +1067,7 @@ StepParams adj_params_from_state(const nlbm_adjoint *a, const float *state)
     kp.uin = kp.gin + pl * 8;
     kp.phi_prev = kp.uin + pl * 2;
     kp.mphi = const_cast<float *>(kp.phi_prev + pl * a->ns);
+    kp.mphi_in = kp.mphi;
     return kp;
 }
 
@@ -1147,11 +1149,8 @@ cudaError_t adj_backward_body(nlbm_adjoint *a)
             kp.gout = out + pl * 9 * ns;
             kp.uout = kp.gout + pl * 8;
             kp.phi = kp.uout + pl * 2;
-            kp.mphi = kp.phi + pl * ns;   // m_phi is updated in place: copy it over first
+            kp.mphi = kp.phi + pl * ns;   // read from the input state, written to the output
             kp.pout = nullptr;
-            if ((e = cudaMemcpyAsync(kp.mphi, in + (kp.mphi - out), pb * 2, cudaMemcpyDeviceToDevice, a->stream)) !=
-                cudaSuccess)
-                return e;
             kp.tape = a->tapes + pl * (size_t)c.tape * (s - 1);
             if ((e = launch_step_tape_b_f32(ns, kp, a->stream)) != cudaSuccess) return e;
         }

@@ -60,7 +60,8 @@ struct StepParams {
     const float *pin;          // 16-bit storage only: P of the previous step
     const float *uin;          // [2][plane] previous step
     float *uout;               // [2][plane] this step
-    float *mphi;               // [2][plane] in: previous step, out: this step
+    float *mphi;               // [2][plane] m_phi of this step (out)
+    const float *mphi_in;      // [2][plane] m_phi of the previous step (equal to mphi: updated in place)
     float *pout;               // [plane] or nullptr
     int model;                 // 0 Model A, 1 Model B (read by the ensemble kernel)
     int row_window;            // ensemble kernel: stage pulls as row windows (see step_tile)

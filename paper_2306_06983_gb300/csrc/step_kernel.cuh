@@ -780,8 +780,8 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             node = (unsigned)y * nx + xg;
 #pragma unroll
             for (int p = 0; p < NS; ++p) php[p] = P.phi_prev[(size_t)p * pl + node];
-            mpx = P.mphi[node];
-            mpy = P.mphi[pl + node];
+            mpx = P.mphi_in[node];
+            mpy = P.mphi_in[pl + node];
         }
         // previous-step velocity of row ra, used by stage B of the next iteration
         // (the ghost sign is applied where the value is used, so that no

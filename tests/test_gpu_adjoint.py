@@ -214,3 +214,48 @@ def test_autograd_function_and_descent():
         out2 = nphase_lbm(phi0, sig - step * sig.grad, mob, p, 200, 50)
         L2 = 0.5 * ((out2.double() - tgt.double()) ** 2).sum()
     assert float(L2) < float(L)
+
+
+def test_taped_sweep_matches_tape_passes():
+    """The reverse sweep takes each step's intermediate fields from the taping
+    forward kernel that rebuilds the segment; the single-step entry point
+    rebuilds them with three separate tape passes over the step's input
+    state.  Over four steps (two segments of two) both give the same tension
+    and mobility gradients, up to the FP32 rounding of the intermediate
+    fields (summation orders differ between the two)."""
+    import torch
+    from paper_2306_06983_gb300.nlbm import AdjointRun, Simulation, pair_list
+    p, phi0 = W.adjoint_problem(32, 32)
+    p0 = with_sigma(p, S0)
+    phi0 = phi0.astype(np.float32)
+    n, every = 4, 2
+    ns = p0["n_phases"] - 1
+    pl = p0["nx"] * p0["ny"]
+    run = AdjointRun(p0, n, every)
+    phiT = run.forward(phi0)
+    seed = (phiT - 1.0 / 3.0).contiguous()
+    _, gs, gm = run.backward(seed)
+    # the input state of every step, from a plain simulation of the same run
+    sim = Simulation(p0)
+    sim.set_phi(phi0)
+    states = []
+    for _ in range(n):
+        states.append(sim.save().view(torch.float32)[:(10 * ns + 12) * pl].clone())
+        sim.step(1)
+    sim.close()
+    # seed of the last step's outputs [f 9(N-1), g 8, phi N-1, u 2, m_phi 2]:
+    # only phi(T), with phase N folded onto the solved phases
+    sd = torch.zeros((10 * ns + 12) * pl, dtype=torch.float32, device=seed.device)
+    sd[(9 * ns + 8) * pl:(10 * ns + 8) * pl] = (seed[:ns] - seed[ns]).reshape(-1)
+    gs_sum, gm_sum = np.zeros_like(gs), 0.0
+    for s in reversed(range(n)):
+        sd, g_s, g_m = run.reverse_step(states[s], sd)
+        gs_sum += g_s
+        gm_sum += g_m
+    run.close()
+    scale = max(abs(gs[a, b]) for a, b in pair_list(ns + 1))
+    for a, b in pair_list(ns + 1):
+        print(f"\nsigma_{a + 1}{b + 1}: sweep {gs[a, b]: .9e}  step by step {gs_sum[a, b]: .9e}", end="")
+        assert abs(gs[a, b] - gs_sum[a, b]) <= 1e-4 * scale, (a, b, gs[a, b], gs_sum[a, b])
+    print(f"\nmobility: sweep {gm: .9e}  step by step {gm_sum: .9e}")
+    assert abs(gm - gm_sum) <= 1e-4 * abs(gm_sum) + 1e-6 * scale, (gm, gm_sum)
