@@ -30,7 +30,7 @@
  * inverted numerically at set-up); the equilibria and source distributions
  * are evaluated per direction from their defining formulas.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Eqs. (18),(21): the collision term is the matrix product
  *    sum_j Lambda_ij (f_j - f_j^eq).
  *  - A unit vector v/|v| is taken as 0 when |v|^2 <= 1e-24.
