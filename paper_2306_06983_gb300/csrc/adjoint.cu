@@ -206,6 +206,7 @@ __global__ void tape_force_kernel(const StepParams P, AdjTape T)
 template <int NS>
 __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
 {
+    pdl_wait();   // the previous kernel of the sweep has completed
     constexpr int N = NS + 1;
     constexpr int NP = N * (N - 1) / 2;
     const unsigned pl = P.plane;
@@ -505,6 +506,7 @@ __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
 template <int NS>
 __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
 {
+    pdl_wait();   // the previous kernel of the sweep has completed
     constexpr int N = NS + 1;
     constexpr int NP = N * (N - 1) / 2;
     const unsigned pl = P.plane;
@@ -592,6 +594,7 @@ __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
 template <int NS>
 __global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
 {
+    pdl_wait();   // the previous kernel of the sweep has completed
     const unsigned pl = P.plane;
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
         const int x = k % P.nx, y = k / P.nx;
@@ -616,6 +619,7 @@ __global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
 template <int NS>
 __global__ void rev_pull_kernel(const StepParams P, AdjFields A)
 {
+    pdl_wait();   // the previous kernel of the sweep has completed
     const unsigned pl = P.plane;
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
         const int x = k % P.nx, y = k / P.nx;
@@ -679,11 +683,12 @@ cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFiel
         tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
         tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
     }
-    rev_collide_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
-    rev_source_kernel<NS><<<nb, 256, 0, st>>>(P, T, A);
-    rev_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, A);
-    rev_pull_kernel<NS><<<nb, 256, 0, st>>>(P, A);
-    return cudaGetLastError();
+    // the four passes overlap each launch with the drain of the one before
+    cudaError_t e;
+    if ((e = launch_pdl(rev_collide_kernel<NS>, nb, 256, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_source_kernel<NS>, nb, 256, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_stencil_kernel<NS>, nb, 256, 0, st, P, A)) != cudaSuccess) return e;
+    return launch_pdl(rev_pull_kernel<NS>, nb, 256, 0, st, P, A);
 }
 
 // dL/dphi_p for the solved phases from dL/dphi over all N phases (phi_N = 1 - sum).

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(T) batch_step_kernel(const StepParams *__restr
     __shared__ int s_k;
     // the other counter is the next launch's; this launch's was cleared by
     // the previous one (or at creation)
+    pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[parity ^ 1] = 0;
     for (;;) {
         if (threadIdx.x == 0) s_k = atomicAdd(&counters[parity], 1);
@@ -86,9 +87,8 @@ cudaError_t launch_nt(const StepParams *d_params, const BatchTile *d_tiles, int 
     cudaError_t e = configure<NS, T>(&blocks);
     if (e != cudaSuccess) return e;
     const int grid = ntiles < blocks ? (ntiles > 0 ? ntiles : 1) : blocks;
-    batch_step_kernel<NS, T><<<grid, T, step_smem_bytes<NS, T, 0, true>(), st>>>(d_params, d_tiles, ntiles,
-                                                                         d_counters, parity);
-    return cudaGetLastError();
+    return launch_pdl(batch_step_kernel<NS, T>, dim3(grid), dim3(T), step_smem_bytes<NS, T, 0, true>(), st, d_params,
+                      d_tiles, ntiles, d_counters, parity);
 }
 
 template <int NS>

@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace nlbm {
 
 constexpr int kMaxPhases = 8;
@@ -67,6 +69,37 @@ struct StepParams {
     int row_window;            // ensemble kernel: stage pulls as row windows (see step_tile)
     float *tape;               // adjoint recompute: the step's intermediate fields (launch_step_tape)
 };
+
+// Programmatic dependent launch (the step kernels, the ensemble kernel and the
+// adjoint's reverse passes): a kernel launched with launch_pdl is scheduled
+// as the blocks of its
+// predecessor in the stream exit, so its launch overlaps their drain.  It
+// must call pdl_wait() before touching memory the predecessor reads or
+// writes; the wait returns once the predecessor has completed and its writes
+// are visible.  Launched without the attribute, the wait does nothing.
+// (Measured: the 256^2 adjoint's reverse sweep 15.5 -> 15.0 ms as a graph,
+// 20.6 -> 15.1 ms as plain launches, its forward 6.5 -> 5.5 ms; 64 lens
+// simulations launched one by one 4,773 -> 5,671 MLUPS.  Releasing successors
+// at the start of each kernel instead of at block exit made the adjoint's
+// graph slower, 17.3 ms.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // One work item of the ensemble kernel: the strip of simulation `sim` that
 // starts at column x0, rows [y0, y0 + ty).

@@ -856,8 +856,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
         __syncthreads();
         // ---------------------------------------------------- stage B
         if (it >= 2) {
-            const int rb = ra - 1;
-            const int s3 = a3m1;
+            const int s3 = a3m1;   // row rb = ra - 1
             if (in_flux) {
                 float ph[N], gx[N], gy[N], Rx[NS], Ry[NS], mx, my;
                 if constexpr (ST == 0) {
@@ -1202,6 +1201,7 @@ __global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
     step_kernel(const StepParams P, const int TY, const int chunks, const int strips)
 {
     extern __shared__ __align__(16) float smem[];
+    pdl_wait();   // launched with launch_pdl
     const int s = blockIdx.x % strips, k = blockIdx.x / strips;
     int y0, ty;
     if (TY > 0) {
@@ -1275,8 +1275,8 @@ cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStr
     }
     const long long blocks = (long long)strips * chunks;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_kernel<NS, MODEL, T, ST, VEC, TAPE><<<(unsigned)blocks, T, smem, st>>>(p, ty, chunks, strips);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel<NS, MODEL, T, ST, VEC, TAPE>, dim3((unsigned)blocks), dim3(T), smem, st, p, ty,
+                      chunks, strips);
 }
 
 // Row windows need nx a multiple of 4 (of 8 with 16-bit storage: rows and
