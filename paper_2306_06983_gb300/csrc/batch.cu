@@ -10,6 +10,8 @@
 // simulations whose pulls are staged as row windows and those that are not.
 // Simulations never exchange data, so no block waits on another; the only
 // cross-block traffic is the tile counter.
+#include <atomic>
+
 #include "step_kernel.cuh"
 
 namespace nlbm {
@@ -58,13 +60,15 @@ cudaError_t configure(int *blocks)
 {
     static_assert(sizeof(StepParams) % sizeof(int) == 0, "parameter block copied as ints");
     const size_t smem = step_smem_bytes<NS, T, 0, true>();
-    static int configured[64] = {0};
-    static int resident[64] = {0};
+    // resident blocks per device, 0 until configured (threads that race here
+    // compute and store the same value)
+    static std::atomic<int> resident[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
+    int r = resident[dev].load(std::memory_order_acquire);
+    if (!r) {
         e = cudaFuncSetAttribute(batch_step_kernel<NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
@@ -72,10 +76,10 @@ cudaError_t configure(int *blocks)
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        resident[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
-        configured[dev] = 1;
+        r = per_sm * sms > 0 ? per_sm * sms : 1;
+        resident[dev].store(r, std::memory_order_release);
     }
-    *blocks = resident[dev];
+    *blocks = r;
     return cudaSuccess;
 }
 

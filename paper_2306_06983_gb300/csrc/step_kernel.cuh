@@ -38,6 +38,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "nlbm_internal.cuh"
 
 namespace nlbm {
@@ -1234,8 +1236,11 @@ template <int NS, int MODEL, int T, int ST, bool VEC, bool TAPE = false>
 cudaError_t variant_slots(int dev, int *out)
 {
     constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
-    static int slots[64] = {0};
-    if (!slots[dev]) {
+    // resident blocks per device, 0 until configured (threads that race here
+    // compute and store the same value)
+    static std::atomic<int> slots[64];
+    int n = slots[dev].load(std::memory_order_acquire);
+    if (!n) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel<NS, MODEL, T, ST, VEC, TAPE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1244,9 +1249,10 @@ cudaError_t variant_slots(int dev, int *out)
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        slots[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+        n = per_sm * sms > 0 ? per_sm * sms : 1;
+        slots[dev].store(n, std::memory_order_release);
     }
-    *out = slots[dev];
+    *out = n;
     return cudaSuccess;
 }
 
