@@ -43,9 +43,18 @@
  *    m_phi(-1) = 0 (it only ever multiplies u(-1)).
  *  - F_c,b = -1/2 sum_a d_a (m_phi,a u_b - u_a m_phi,b).
  *  - rho_0 in lambda_0 is taken as 0 (g_0 feeds no macroscopic quantity).
- *  - F_g = 0 (no gravity).
+ *  - F_g = rho g (gravity as a body force per unit volume, Sec. 2.2).
  *  - Wall ghosts for stencils: phi mirrored, u negated (no slip), m_phi
- *    reflected (normal component negated).
+ *    reflected (normal component negated).  At a wetting y wall (Sec. 4.2:
+ *    n_w . grad phi_p = sum_{q != p} (4/eps) phi_p phi_q cos theta_pq, the
+ *    pairwise angles from the N-1 given cos theta_pN by Young's relation,
+ *    n_w the fluid's outward normal, pointing into the wall: an acute
+ *    theta_pq makes phase p spread) the ghost row at distance k = 1, 2 is
+ *    its mirror image plus (2k - 1) s_p, s_p that right-hand side at the
+ *    image node, so that the difference across the wall (ghost minus first
+ *    row) equals s_p; m_phi at such a ghost node is
+ *    evaluated there from the ghost phase fields (Eqs. (3), (13)).  With all
+ *    cos theta_pN = 0 this is the plain mirror (no-flux).
  *  - Initial state: f_i = w_i phi_p, g_i = lambda_i(P=0), u = 0, P = 0.
  */
 #include <math.h>
@@ -100,6 +109,9 @@ typedef struct {
     double sigma[MAXN * MAXN];
     double unit_delta;  /* 0: unit vectors read as 0 when |v|^2 <= 1e-24; > 0: the
                            smooth reading v / sqrt(|v|^2 + delta^2) */
+    double gx, gy;      /* gravity g: F_g = rho g */
+    double wall_cos[2 * MAXN]; /* cos theta_pN, p < N-1, of the wall at y = 0
+                           ([p]) and at y = ny - 1 ([MAXN + p]); 0 = no-flux */
 } or_params;
 
 typedef struct {
@@ -108,6 +120,8 @@ typedef struct {
     size_t n;           /* nodes */
     real Mm[Q][Q], Mi[Q][Q];
     real tau_f;
+    int wet;            /* a y wall with some cos theta_pN != 0 */
+    real wc[2][MAXN][MAXN]; /* (4/eps) cos theta_pq of the two y walls */
     long long steps;
     /* state */
     real *f, *fn;     /* [L][Q][n] post-streaming populations, spare */
@@ -181,6 +195,45 @@ static void fetch_vec(const or_sim *s, const real *V, int x, int y, int kind,
     }
     *vx = a;
     *vy = b;
+}
+
+/* Phase field p at (x, y), ghosts included (the wetting ghost rows are
+ * described at the top of this file). */
+static real fetch_phi(const or_sim *s, int p, int x, int y)
+{
+    int fx, fy;
+    int xx = map_coord(x, s->p.nx, s->p.wall_x, &fx);
+    int yy = map_coord(y, s->p.ny, s->p.wall_y, &fy);
+    size_t k = nid(s, xx, yy);
+    real v = s->phi[p * s->n + k];
+    if (s->wet && fy) {
+        const int w = y < 0 ? 0 : 1;
+        const int d = y < 0 ? -y : y - (s->p.ny - 1);
+        real sp = 0;
+        for (int q = 0; q < s->N; q++) sp += s->wc[w][p][q] * s->phi[q * s->n + k];
+        v += (2 * d - 1) * v * sp;
+    }
+    return v;
+}
+
+/* Eq. (27) on phase field p (ghosts from fetch_phi). */
+static void grad_phi_at(const or_sim *s, int p, int x, int y, real *gx, real *gy)
+{
+    real ax = 0, ay = 0;
+    for (int i = 1; i < Q; i++) {
+        real v = fetch_phi(s, p, x + CX[i], y + CY[i]);
+        ax += W[i] * CX[i] * v;
+        ay += W[i] * CY[i] * v;
+    }
+    *gx = ax / CS2;
+    *gy = ay / CS2;
+}
+
+static real lap_phi_at(const or_sim *s, int p, int x, int y)
+{
+    real c0 = fetch_phi(s, p, x, y), a = 0;
+    for (int i = 1; i < Q; i++) a += 2.0 * W[i] * (fetch_phi(s, p, x + CX[i], y + CY[i]) - c0);
+    return a / CS2;
 }
 
 /* Sec. 3, Eq. (27): grad chi = sum_{i!=0} w_i c_i chi(x+c_i) / (c_s^2 dt). */
@@ -401,6 +454,13 @@ static int valid(const or_params *p)
     if ((p->wall_x && p->nx < 4) || (p->wall_y && p->ny < 4)) return 0;
     if (!(p->eps > 0) || !(p->mobility > 0)) return 0;
     if (!(p->unit_delta >= 0) || !isfinite(p->unit_delta)) return 0;
+    if (!isfinite(p->gx) || !isfinite(p->gy)) return 0;
+    for (int w = 0; w < 2; w++)
+        for (int a = 0; a < MAXN; a++) {
+            double c = p->wall_cos[w * MAXN + a];
+            if (!(fabs(c) <= 1.0)) return 0;
+            if (c != 0 && (!p->wall_y || a >= p->n_phases - 1)) return 0;
+        }
     if (p->model != 0 && p->model != 1) return 0;
     if (p->model == 0 && !(p->model_a_n > 0)) return 0;
     for (int a = 0; a < p->n_phases; a++) {
@@ -436,6 +496,24 @@ void *or_create(const or_params *p)
     s->n = (size_t)p->nx * p->ny;
     /* Sec. 3, Eq. (20): M = (tau_f - 0.5) c_s^2 dt. */
     s->tau_f = 0.5 + p->mobility / CS2;
+    /* Sec. 4.2: cos theta_pq from the N-1 angles against phase N (Young's
+     * relation), cos theta_qp = -cos theta_pq; stored times 4/eps. */
+    for (int w = 0; w < 2; w++) {
+        const int N = s->N;
+        const double *cn = p->wall_cos + w * MAXN;
+        for (int a = 0; a < N; a++)
+            for (int b = 0; b < N; b++) {
+                double c = 0;
+                if (a != b) {
+                    if (b == N - 1) c = cn[a];
+                    else if (a == N - 1) c = -cn[b];
+                    else c = (p->sigma[a * MAXN + N - 1] * cn[a] - p->sigma[b * MAXN + N - 1] * cn[b]) /
+                             p->sigma[a * MAXN + b];
+                }
+                s->wc[w][a][b] = (real)(4.0 / p->eps * c);
+                if (c != 0) s->wet = 1;
+            }
+    }
     build_M(s->Mm);
     if (invert9(s->Mm, s->Mi)) {
         or_destroy(s);
@@ -574,6 +652,28 @@ static void stream_store16(or_sim *s)
 }
 #endif
 
+/* m_phi (Eq. (13)) at a ghost node beyond a wetting wall, evaluated there
+ * from the ghost phase fields: their gradients (Eq. (27)) and sources
+ * (Eqs. (2)-(4)). */
+static void mphi_ghost(const or_sim *s, int x, int y, real *mx, real *my)
+{
+    const or_params *pp = &s->p;
+    const int N = s->N;
+    real ph[MAXN], gp[MAXN][2], R[MAXN][2];
+    for (int p = 0; p < N; p++) {
+        ph[p] = fetch_phi(s, p, x, y);
+        grad_phi_at(s, p, x, y, &gp[p][0], &gp[p][1]);
+    }
+    source_at(pp, N, ph, (const real(*)[2])gp, R);
+    real ax = 0, ay = 0;
+    for (int p = 0; p < N; p++) {
+        ax -= pp->rho[p] * pp->mobility * (gp[p][0] - R[p][0]);
+        ay -= pp->rho[p] * pp->mobility * (gp[p][1] - R[p][1]);
+    }
+    *mx = ax;
+    *my = ay;
+}
+
 static void step_once(or_sim *s)
 {
     const int nx = s->p.nx, ny = s->p.ny, N = s->N, L = s->L;
@@ -602,22 +702,24 @@ static void step_once(or_sim *s)
         s->mu[k] = m;
     }
 
-    /* Sec. 3, Eq. (27): gradients and Laplacians of every phi_p, grad rho. */
+    /* Sec. 3, Eq. (27): gradients and Laplacians of every phi_p, and
+     * grad rho = sum_p rho_p grad phi_p (Eq. (11) is linear in phi). */
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t k = nid(s, x, y);
+            real grx = 0, gry = 0;
             for (int p = 0; p < N; p++) {
                 real gx, gy;
-                grad_at(s, s->phi + p * n, x, y, &gx, &gy);
+                grad_phi_at(s, p, x, y, &gx, &gy);
                 s->grad[(p * 2 + 0) * n + k] = gx;
                 s->grad[(p * 2 + 1) * n + k] = gy;
-                s->lap[p * n + k] = lap_at(s, s->phi + p * n, x, y);
+                s->lap[p * n + k] = lap_phi_at(s, p, x, y);
+                grx += pp->rho[p] * gx;
+                gry += pp->rho[p] * gy;
             }
-            real gx, gy;
-            grad_at(s, s->rho, x, y, &gx, &gy);
-            s->gradrho[k] = gx;
-            s->gradrho[n + k] = gy;
+            s->gradrho[k] = grx;
+            s->gradrho[n + k] = gry;
         }
 
     /* Sec. 2.1, Eqs. (2)-(4): sources; Sec. 2.2, Eq. (13): m_phi;
@@ -660,7 +762,7 @@ static void step_once(or_sim *s)
     }
 
     /* Sec. 3, text after Eq. (24): F_c = -div(m_phi u - u m_phi)/2 with the
-     * lagged velocity; total force F = F_s + F_g + F_c with F_g = 0. */
+     * lagged velocity; total force F = F_s + F_g + F_c with F_g = rho g. */
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
@@ -668,15 +770,19 @@ static void step_once(or_sim *s)
             real div[2] = {0, 0};
             for (int i = 1; i < Q; i++) {
                 real mx, my, ux, uy;
-                fetch_vec(s, s->mphi, x + CX[i], y + CY[i], K_REFLECT, &mx, &my);
+                const int yn = y + CY[i];
+                if (s->wet && (yn < 0 || yn >= ny))
+                    mphi_ghost(s, x + CX[i], yn, &mx, &my);
+                else
+                    fetch_vec(s, s->mphi, x + CX[i], yn, K_REFLECT, &mx, &my);
                 fetch_vec(s, s->u_prev, x + CX[i], y + CY[i], K_VELOCITY, &ux, &uy);
                 real m[2] = {mx, my}, u[2] = {ux, uy}, c[2] = {(real)CX[i], (real)CY[i]};
                 for (int b = 0; b < 2; b++)
                     for (int a = 0; a < 2; a++)
                         div[b] += W[i] * c[a] * (m[a] * u[b] - u[a] * m[b]) / CS2;
             }
-            s->F[k] += -0.5 * div[0];
-            s->F[n + k] += -0.5 * div[1];
+            s->F[k] += -0.5 * div[0] + s->rho[k] * pp->gx;
+            s->F[n + k] += -0.5 * div[1] + s->rho[k] * pp->gy;
         }
 
     /* Macroscopic velocity and pressure, Eqs. (25b),(25c); collisions,

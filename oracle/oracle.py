@@ -6,7 +6,10 @@ compiled here with the host compiler (gcc, OpenMP) into ``oracle/_build``.
 
 Parameters are passed as a plain dict with the keys the workload generator
 produces: nx, ny, n_phases, model ('A' or 'B'), model_a_n, eps, mobility,
-rho[N], mu[N] (dynamic viscosities), sigma[N][N], wall_x, wall_y.
+rho[N], mu[N] (dynamic viscosities), sigma[N][N], wall_x, wall_y, and
+optionally unit_delta, gx, gy (gravity, F_g = rho g) and wall_cos (2 (N-1)
+cosines of the contact angles against phase N at the walls y = 0 and
+y = ny - 1, Sec. 4.2).
 """
 
 from __future__ import annotations
@@ -41,6 +44,8 @@ class params_struct(ctypes.Structure):
         ("rho", ctypes.c_double * MAXN), ("mu", ctypes.c_double * MAXN),
         ("sigma", ctypes.c_double * (MAXN * MAXN)),
         ("unit_delta", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("wall_cos", ctypes.c_double * (2 * MAXN)),
     ]
 
 
@@ -127,6 +132,16 @@ def make_params(p: dict, solve_all: bool = False, store16: int = 0) -> params_st
     s.model_a_n = float(p.get("model_a_n", 1.0))
     s.eps, s.mobility = float(p["eps"]), float(p["mobility"])
     s.unit_delta = float(p.get("unit_delta", 0.0))
+    s.gx, s.gy = float(p.get("gx", 0.0)), float(p.get("gy", 0.0))
+    # wetting: cos theta_pN of the wall at y = 0 (first N-1) and at y = ny - 1
+    wc = p.get("wall_cos")
+    if wc is not None:
+        wc = [float(v) for v in wc]
+        if len(wc) != 2 * (N - 1):
+            raise ValueError("wall_cos holds 2 (N - 1) cosines")
+        for a in range(N - 1):
+            s.wall_cos[a] = wc[a]
+            s.wall_cos[MAXN + a] = wc[N - 1 + a]
     sig = np.asarray(p["sigma"], dtype=np.float64).reshape(N, N)
     for a in range(N):
         s.rho[a] = float(p["rho"][a])
