@@ -12,9 +12,10 @@ population buffers (604 MB each) are larger than L2, so no flush is needed.
 
 Beside the headline the line carries "forms": the same workload with
 bfloat16 / binary16 population storage (throughput, roofline fraction and
-distance to the FP32 fields after the same steps) and the 64-member lens
+distance to the FP32 fields after the same steps), the 64-member lens
 ensemble advanced in one persistent launch per step (against one launch per
-member).
+member), the ternary Rayleigh-Taylor instability (gravity and walls) and the
+differentiated run (forward and reverse sweep of the adjoint).
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (weak scaling, no collective on the data path); rank 0 prints one
@@ -213,9 +214,10 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
     """The other forms of the method, each timed with CUDA events over
     args.steps steps after args.warmup, beside the headline (FP32) run:
     16-bit population storage on the same workload (with its distance to the
-    FP32 fields after the same steps), and the 64-member lens ensemble in one
+    FP32 fields after the same steps), the 64-member lens ensemble in one
     persistent launch per step (autotuned tile shape, graph replays) against
-    one launch per member."""
+    one launch per member, the ternary Rayleigh-Taylor instability (gravity,
+    walls) and the adjoint."""
     import torch
     from paper_2306_06983_gb300 import workloads as W
     from paper_2306_06983_gb300.nlbm import Batch, Simulation
@@ -296,8 +298,36 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         }
         del sims
         torch.cuda.empty_cache()
+        forms["rti"] = measure_rti(args, timed, stream, peak)
         forms["adjoint"] = measure_adjoint(timed)
     return forms
+
+
+def measure_rti(args, timed, stream, peak):
+    """Gravity and walls: the ternary Rayleigh-Taylor instability (Sec. 4.4,
+    256 x 1024, rho 3:2:1, F_g = rho g), FP32, one launch per step, timed with
+    CUDA events like the headline; with the volume drift over the run."""
+    from paper_2306_06983_gb300 import workloads as W
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.rayleigh_taylor(d=256)
+    sim = Simulation(p, stream=stream)
+    sim.set_phi(phi0.astype(np.float32))
+    m0 = sim.phase_mass()
+    sim.step(args.warmup)
+    l0 = sim.kernel_launches
+    ms = timed(stream, sim.step, args.steps)
+    launches = sim.kernel_launches - l0
+    drift = float((np.abs(sim.phase_mass() - m0) / np.abs(m0)).max())
+    sim.close()
+    nodes = p["nx"] * p["ny"]
+    bpl = bytes_per_lup(3)
+    return {
+        "workload": "ternary Rayleigh-Taylor instability 256x1024, rho 3:2:1, At 0.5, Re 1000, Ca 0.28, "
+                    "sqrt(g d) = 0.04, walls top and bottom, Model B, FP32",
+        "nodes": nodes, "value": round(nodes / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
+        "algorithmic_bytes_per_lup": bpl, "roofline_frac": round(bpl * nodes / (ms / 1e3) / 1e9 / peak, 4),
+        "gpu_launches": launches, "mass_drift_rel": drift,
+    }
 
 
 def measure_adjoint(timed):

@@ -81,7 +81,9 @@ typedef struct nlbm_params {
     const double *mu;      /* [N] dynamic viscosities > 0 (Eq. (12)), host */
     const double *sigma;   /* [N*N] pairwise surface tensions, symmetric,
                               zero diagonal, > 0 off it (Eq. (15)), host */
-    double gx, gy;         /* body acceleration; must be 0 (else ENOTSUP) */
+    double gx, gy;         /* gravity g: the body force F_g = rho g enters the
+                              total force F = F_s + F_g + F_c (Sec. 2.2, Sec. 3);
+                              finite */
     int32_t storage;       /* nlbm_storage */
     int32_t reserved;      /* must be 0 */
     double unit_delta;     /* >= 0.  Unit vectors of the sources (n_p of
@@ -90,6 +92,18 @@ typedef struct nlbm_params {
                               open); > 0 uses the smooth v / sqrt(|v|^2 +
                               delta^2), which is what a differentiated run
                               needs (see nlbm_adjoint_create) */
+    const double *wall_cos;/* NULL, or [2(N-1)] host memory: wetting walls on
+                              y (Sec. 4.2, n_w . grad phi_p = sum_{q != p}
+                              (4/eps) phi_p phi_q cos theta_pq, n_w pointing
+                              into the wall).  Entries 0..N-2 are cos theta_pN
+                              (contact angle of phase p against phase N,
+                              measured in phase p) of the wall at y = 0,
+                              entries N-1..2N-3 those of the wall at
+                              y = ny - 1; the pairwise angles follow from
+                              Young's relation.  Each |cos| <= 1; nonzero
+                              needs bc_y = NLBM_BC_WALL (EINVAL otherwise).
+                              NULL or zeros: neutral no-flux walls.  Walls on
+                              x stay neutral. */
 } nlbm_params;
 
 typedef struct nlbm_sim nlbm_sim;

@@ -112,7 +112,15 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
     if (p->reserved != 0) { set_err(err, "reserved must be 0"); return NLBM_EINVAL; }
     if (!std::isfinite(p->unit_delta) || p->unit_delta < 0.0) { set_err(err, "unit_delta must be >= 0"); return NLBM_EINVAL; }
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) { set_err(err, "gravity not finite"); return NLBM_EINVAL; }
-    if (p->gx != 0.0 || p->gy != 0.0) { set_err(err, "gravity is not supported"); return NLBM_ENOTSUP; }
+    bool wet = false;
+    if (p->wall_cos) {
+        for (int a = 0; a < 2 * (N - 1); ++a) {
+            const double c = p->wall_cos[a];
+            if (!(std::fabs(c) <= 1.0)) { set_err(err, "wall_cos[%d] must lie in [-1, 1]", a); return NLBM_EINVAL; }
+            if (c != 0.0) wet = true;
+        }
+        if (wet && p->bc_y != NLBM_BC_WALL) { set_err(err, "wall_cos needs walls on y"); return NLBM_EINVAL; }
+    }
     if (p->storage != NLBM_STORE_F32 && !is_half(p->storage)) { set_err(err, "unknown storage"); return NLBM_EINVAL; }
     if (is_half(p->storage) && (p->nx & 1)) {
         set_err(err, "16-bit storage needs an even nx (got %d)", p->nx); return NLBM_EINVAL;
@@ -145,6 +153,24 @@ nlbm_status validate(const nlbm_params *p, StepParams *kp, char *err)
         kp->mob = (float)p->mobility;
         kp->s1 = (float)(1.0 / (0.5 + 3.0 * p->mobility));        // Eq. (20), c_s^2 = 1/3
         kp->model_n = (float)p->model_a_n;
+        kp->gx = (float)p->gx;
+        kp->gy = (float)p->gy;
+        // Sec. 4.2: cos theta_pq from the N-1 angles against phase N by
+        // Young's relation, cos theta_qp = -cos theta_pq; stored times 4/eps
+        kp->wet = wet ? 1 : 0;
+        for (int w = 0; wet && w < 2; ++w) {
+            const double *cn = p->wall_cos + w * (N - 1);
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) {
+                    double c = 0.0;
+                    if (a != b) {
+                        if (b == N - 1) c = cn[a];
+                        else if (a == N - 1) c = -cn[b];
+                        else c = (p->sigma[a * N + N - 1] * cn[a] - p->sigma[b * N + N - 1] * cn[b]) / p->sigma[a * N + b];
+                    }
+                    kp->wetc[w][a][b] = (float)(4.0 / p->eps * c);
+                }
+        }
         const double n = p->model_a_n;
         kp->model_n_int = (n == std::floor(n) && n >= 1.0 && n <= 8.0) ? (int)n : 0;
     }
@@ -988,8 +1014,8 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
     nlbm_status st = validate(p, nullptr, err);
     if (st != NLBM_OK) return st;
     if (p->model != NLBM_MODEL_B || p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC ||
-        p->storage != NLBM_STORE_F32) {
-        set_err(err, "the adjoint covers Model B on a periodic lattice with FP32 storage");
+        p->storage != NLBM_STORE_F32 || p->gx != 0.0 || p->gy != 0.0) {
+        set_err(err, "the adjoint covers Model B on a periodic lattice with FP32 storage and no gravity");
         return NLBM_ENOTSUP;
     }
     if (nsteps < 1 || every < 1) { set_err(err, "nsteps and checkpoint interval must be >= 1"); return NLBM_EINVAL; }

@@ -68,6 +68,9 @@ struct StepParams {
     int model;                 // 0 Model A, 1 Model B (read by the ensemble kernel)
     int row_window;            // ensemble kernel: stage pulls as row windows (see step_tile)
     float *tape;               // adjoint recompute: the step's intermediate fields (launch_step_tape)
+    float gx, gy;              // gravity: F_g = rho g
+    int wet;                   // a y wall has a contact angle other than 90 degrees
+    float wetc[2][kMaxPhases][kMaxPhases];   // (4/eps) cos theta_pq, walls y = 0 and y = ny - 1
 };
 
 // Programmatic dependent launch (the step kernels, the ensemble kernel and the

@@ -814,6 +814,27 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             } else {
                 sum_pulled16<NS, ST, true>(s_F, T, t, par_cur, ph, plo, jx, jy);
             }
+            if (P.wet && (ra < 0 || ra >= P.ny)) {
+                // ghost row beyond a wetting wall (Sec. 4.2): its mirror image
+                // plus (2k - 1) s_p, s_p = phi_p sum_q (4/eps) cos theta_pq phi_q
+                // at the image node, so that the difference across the wall
+                // is s_p (n_w pointing into the wall)
+                const int w = ra < 0 ? 0 : 1;
+                const float k2 = (float)(2 * (ra < 0 ? -ra : ra - (P.ny - 1)) - 1);
+                float phN = 1.f;
+#pragma unroll
+                for (int p = 0; p < NS; ++p) phN -= ph[p];
+                float sp[NS];
+#pragma unroll
+                for (int p = 0; p < NS; ++p) {
+                    float a = P.wetc[w][p][NS] * phN;
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) a += P.wetc[w][p][q] * ph[q];
+                    sp[p] = ph[p] * a;
+                }
+#pragma unroll
+                for (int p = 0; p < NS; ++p) ph[p] += k2 * sp[p];
+            }
             const int s5 = a5;
 #pragma unroll
             for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
@@ -957,6 +978,9 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                 Fx += 0.5f * dyw;
                 Fy -= 0.5f * dxw;
             }
+            // gravity: F_g = rho g (total force F = F_s + F_g + F_c)
+            Fx += rho * P.gx;
+            Fy += rho * P.gy;
 
             // macroscopic velocity (Eq. (25b)) and mass flux (Eq. (13))
             if constexpr (V16) {

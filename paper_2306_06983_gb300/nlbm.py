@@ -49,6 +49,7 @@ class nlbm_params(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("unit_delta", ctypes.c_double),
+        ("wall_cos", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -159,7 +160,14 @@ def make_params(p: dict):
     s.storage = STORAGE_CODES[st] if isinstance(st, str) else int(st)
     s.reserved = 0
     s.unit_delta = float(p.get("unit_delta", 0.0))
-    return s, (rho, mu, sigma)
+    wc = p.get("wall_cos")
+    wall_cos = None
+    if wc is not None:
+        wall_cos = (ctypes.c_double * len(wc))(*[float(v) for v in wc])
+        if len(wc) != 2 * (N - 1):
+            raise ValueError("wall_cos holds 2 (N - 1) cosines")
+        s.wall_cos = ctypes.cast(wall_cos, ctypes.POINTER(ctypes.c_double))
+    return s, (rho, mu, sigma, wall_cos)
 
 
 # ------------------------------------------------- one-to-one C entry points

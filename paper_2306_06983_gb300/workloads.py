@@ -257,3 +257,60 @@ def adjoint_problem(nx=256, ny=256, seed=SEED, sigma=(0.01, 0.01, 0.01), unit_de
     p = base_params(nx, ny, 3, model="B", sigma=[[0.0, s12, s13], [s12, 0.0, s23], [s13, s23, 0.0]])
     p["unit_delta"] = float(unit_delta)
     return p, phi0
+
+
+def compound_droplet(theta23, theta13=75.0, nx=300, ny=150, R=60.0, eps=5.0, sigma=0.01,
+                     mobility=0.1, rho=(1.0, 0.5, 0.001), mu=(0.1, 0.05, 1e-4), model="B",
+                     model_a_n=1.0):
+    """Compound droplet spreading on a solid wall (Sec. 4.2): a half-disk of
+    radius R on the bottom wall of [-nx/2, nx/2] x [0, ny], its left half
+    phase 1 and its right half phase 2, in phase 3; periodic in x, the bottom
+    wall wetting with contact angles theta13 and theta23 (degrees, against
+    phase 3), the top wall no-flux.  Profiles as in Sec. 4.2:
+    phi_1 = D (0.5 - 0.5 tanh(2x/eps)), phi_2 = D (0.5 + 0.5 tanh(2x/eps)),
+    D = 0.5 + 0.5 tanh((R - r)/(eps/2)).  Material properties of the ternary
+    system of Sec. 4.1 (rho 1000:500:1, mu 100:50:0.1, scaled so that every
+    kinematic viscosity is 0.1), sigma_pq = 0.01, eps = 5; the mobility is
+    not given there (0.1 here).  Node (i, j) sits at x = i + 1/2 - nx/2,
+    y = j + 1/2 above the wall."""
+    x = np.arange(nx, dtype=np.float64)[None, :] + 0.5 - nx / 2.0
+    y = np.arange(ny, dtype=np.float64)[:, None] + 0.5
+    D = 0.5 + 0.5 * np.tanh((R - np.sqrt(x ** 2 + y ** 2)) / (eps / 2.0))
+    phi1 = D * (0.5 - 0.5 * np.tanh(2.0 * x / eps))
+    phi2 = D * (0.5 + 0.5 * np.tanh(2.0 * x / eps))
+    p = base_params(nx, ny, 3, model=model, model_a_n=model_a_n, eps=eps, mobility=mobility,
+                    rho=list(rho), mu=list(mu), sigma=sigma, wall_y=True)
+    c13, c23 = np.cos(np.radians(theta13)), np.cos(np.radians(theta23))
+    p["wall_cos"] = [float(c13), float(c23), 0.0, 0.0]
+    return p, np.stack([phi1, phi2])
+
+
+def rayleigh_taylor(d=256, ternary=True, eps=4.0, mobility=0.1, model="B", model_a_n=1.0,
+                    sqrt_gd=0.04):
+    """Rayleigh-Taylor instability (Sec. 4.4) on [-d/2, d/2] x [-2d, 2d]
+    (d x 4d nodes), periodic in x, no-flux walls at the bottom and top, the
+    heavy fluid 1 on top.  At = 0.5, Re = d rho_3 sqrt(g d) / mu_3 = 1000,
+    Ca = mu_3 sqrt(g d) / sigma = 0.28, rho_1 : rho_2 : rho_3 = 3 : 2 : 1,
+    equal viscosities, gravity (0, -g).  The lattice velocity scale
+    sqrt(g d) (0.04 here), eps and the mobility are not given (readings).
+    Ternary: phi_1 = 0.5 + 0.5 tanh((y - 2d/3 - 0.1 d sin(2 pi x/d))/(eps/2)),
+    phi_2 = (1 - phi_1)(0.5 + 0.5 tanh((y + 2d/3 + 0.1 d sin(2 pi x/d))/(eps/2)));
+    binary (phi_2 = 0): phi_1 = 0.5 + 0.5 tanh((y - 0.1 d cos(2 pi x/d))/(eps/2)).
+    Node (i, j) sits at x = i + 1/2 - d/2, y = j + 1/2 - 2d."""
+    nx, ny = int(d), int(4 * d)
+    x = np.arange(nx, dtype=np.float64)[None, :] + 0.5 - d / 2.0
+    y = np.arange(ny, dtype=np.float64)[:, None] + 0.5 - 2.0 * d
+    if ternary:
+        s = 0.1 * d * np.sin(2 * np.pi * x / d)
+        phi1 = 0.5 + 0.5 * np.tanh((y - 2 * d / 3 - s) / (eps / 2.0))
+        phi2 = (1.0 - phi1) * (0.5 + 0.5 * np.tanh((y + 2 * d / 3 + s) / (eps / 2.0)))
+    else:
+        phi1 = 0.5 + 0.5 * np.tanh((y - 0.1 * d * np.cos(2 * np.pi * x / d)) / (eps / 2.0))
+        phi2 = np.zeros_like(phi1)
+    g = sqrt_gd ** 2 / d
+    mu3 = d * 1.0 * sqrt_gd / 1000.0
+    sigma = mu3 * sqrt_gd / 0.28
+    p = base_params(nx, ny, 3, model=model, model_a_n=model_a_n, eps=eps, mobility=mobility,
+                    rho=[3.0, 2.0, 1.0], mu=[mu3, mu3, mu3], sigma=sigma, wall_y=True)
+    p["gy"] = -g
+    return p, np.stack([phi1, phi2])

@@ -77,9 +77,12 @@ def test_workspace_bytes_of_16bit_storage(lib):
 @pytest.mark.parametrize("mutate,status", [
     (dict(n_phases=1), 1), (dict(n_phases=9), 1), (dict(nx=0), 1), (dict(eps=0.0), 1),
     (dict(eps=float("nan")), 1), (dict(mobility=-0.1), 1), (dict(model="A", model_a_n=0.0), 1),
-    (dict(gx=1e-5), 4), (dict(storage=1, nx=63), 1), (dict(storage="f16", nx=65), 1),
+    (dict(gx=float("nan")), 1), (dict(storage=1, nx=63), 1), (dict(storage="f16", nx=65), 1),
     (dict(storage=7), 1),
     (dict(wall_y=True, ny=3), 1),
+    (dict(wall_cos=[0.5, 0.0, 0.0, 0.0]), 1),                 # wetting needs walls on y
+    (dict(wall_y=True, wall_cos=[1.5, 0.0, 0.0, 0.0]), 1),   # |cos| <= 1
+    (dict(wall_y=True, wall_cos=[0.0, 0.0, float("nan"), 0.0]), 1),
 ])
 def test_parameter_validation(lib, mutate, status):
     from paper_2306_06983_gb300 import nlbm
@@ -94,6 +97,23 @@ def test_parameter_validation(lib, mutate, status):
     with pytest.raises(nlbm.NlbmError) as ei:
         nlbm.nlbm_workspace_bytes(q)
     assert ei.value.status == status
+
+
+def test_gravity_and_wetting_walls_are_accepted(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    base = nlbm.nlbm_workspace_bytes(dict(p, wall_y=True))
+    q = dict(p, wall_y=True, gx=1e-6, gy=-2e-5, wall_cos=[0.5, -0.25, 0.0, 1.0])
+    assert nlbm.nlbm_workspace_bytes(q) == base
+
+
+def test_adjoint_refuses_gravity(lib):
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.adjoint_problem(32, 32)
+    nlbm.nlbm_adjoint_workspace_bytes(p, 10, 5)
+    with pytest.raises(nlbm.NlbmError) as ei:
+        nlbm.nlbm_adjoint_workspace_bytes(dict(p, gy=1e-5), 10, 5)
+    assert ei.value.status == 4
 
 
 def test_sigma_must_be_symmetric_positive(lib):
