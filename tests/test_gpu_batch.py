@@ -32,8 +32,8 @@ def f32(a):
 
 
 def mixed_members():
-    """Members of different sizes (ragged, multiple of 4, tiny), boundaries,
-    models and exponents; N = 3 for all."""
+    """Members of different sizes (ragged, multiple of 4, tiny), boundaries
+    (wetting walls too), gravity, models and exponents; N = 3 for all."""
     return [
         W.random_smooth(67, 45, 3, seed=21, model="B"),
         W.random_smooth(64, 64, 3, seed=22, model="A", model_a_n=1.0),
@@ -43,6 +43,10 @@ def mixed_members():
         W.lens(96, 48, 9.6, 0.01, 0.012, 0.007, model="B"),
         W.random_smooth(8, 8, 3, seed=25, model="B", n_disks=1),
         W.random_smooth(200, 71, 3, seed=26, model="A", model_a_n=3.0, wall_x=True, wall_y=True),
+        # wetting walls on y and gravity (Sec. 4.2, F_g = rho g)
+        (lambda q: (dict(q[0], wall_cos=[0.5, -0.3, 0.2, 0.6], gy=-1e-5), q[1]))(
+            W.random_smooth(96, 40, 3, seed=27, model="B", wall_y=True)),
+        (lambda q: (dict(q[0], gx=3e-6, gy=1e-6), q[1]))(W.random_smooth(64, 48, 3, seed=28, model="A")),
     ]
 
 
