@@ -137,7 +137,13 @@ def _check(st: int, handle=None):
 
 
 def make_params(p: dict):
-    """ctypes parameter block from a workload dict; returns (struct, keepalive)."""
+    """ctypes parameter block from a workload dict; returns (struct, keepalive).
+
+    Keys: nx, ny, n_phases, model ('A' or 'B'), eps, mobility, rho[N], mu[N],
+    sigma[N][N]; optional model_a_n, wall_x, wall_y, storage ('f32', 'bf16',
+    'f16'), unit_delta, gx, gy (gravity, F_g = rho g) and wall_cos (2 (N-1)
+    cosines of the contact angles against phase N at the walls y = 0 and
+    y = ny - 1; see nlbm_params in include/nlbm.h)."""
     N = int(p["n_phases"])
     rho = (ctypes.c_double * N)(*[float(v) for v in p["rho"]])
     mu = (ctypes.c_double * N)(*[float(v) for v in p["mu"]])
