@@ -193,6 +193,20 @@ def test_compound_droplet_wetted_lengths(theta23):
     assert np.all(np.abs(g[0][3] - m0) / np.abs(m0) < 1e-6)
 
 
+@pytest.mark.parametrize("theta23,n", [(60.0, 1.0), (60.0, 2.0), (90.0, 1.0), (90.0, 2.0)])
+def test_compound_droplet_model_a(theta23, n):
+    """The same with Model A (the table's other columns), 100,000 steps."""
+    L1a, L2a = golden_wetting()[theta23]
+    p, phi0 = W.compound_droplet(theta23, rho=(1.0, 1.0, 1.0), mu=(0.1, 0.1, 0.1), model="A",
+                                 model_a_n=n)
+    m0, g = gpu_run(p, f32(phi0), [100000])
+    phi = g[0][0]
+    L1, L2 = crossing_length(phi[0][0]) / 60.0, crossing_length(phi[1][0]) / 60.0
+    print(f"\nModel A n={n} theta23 {theta23}: L1 {L1:.4f} ({L1a}), L2 {L2:.4f} ({L2a})")
+    assert abs(L1 / L1a - 1) < 0.03 and abs(L2 / L2a - 1) < 0.03
+    assert np.all(np.abs(g[0][3] - m0) / np.abs(m0) < 1e-6)
+
+
 def test_compound_droplet_with_the_papers_densities():
     """The same with the paper's density ratio of 1000 (rho 1 : 0.5 : 0.001,
     kinematic viscosities 0.1), theta_23 = 60 degrees."""
