@@ -259,6 +259,32 @@ def adjoint_problem(nx=256, ny=256, seed=SEED, sigma=(0.01, 0.01, 0.01), unit_de
     return p, phi0
 
 
+def static_droplets(N=4, model="B", model_a_n=1.0, absent=(), nx=300, ny=100, R=20.0, eps=5.0,
+                    sigma=0.01, mobility=0.01):
+    """Static droplets (Sec. 4.1): drops of radius R of phases 1..N-1 centred
+    at x = -100, 0, 100 (the first N-1 of them) on the centre line of the
+    periodic domain [-nx/2, nx/2] x [-ny/2, ny/2], phase N around them,
+    phi_p = 0.5 + 0.5 tanh((R - |x - x_p|)/(eps/2)).  Densities and
+    viscosities 1000:500:100:1 and 100:50:10:0.1 for the quaternary system;
+    the ternary and binary systems keep those of phases 1, 2 and of phase 1
+    with the last entry for phase N.  Phases listed in absent (1-based) are
+    zero everywhere (the reduction check).  The mobility is not given in the
+    paper (0.01 here).  Node (i, j) sits at x = i + 1/2 - nx/2,
+    y = j + 1/2 - ny/2."""
+    centres = [-100.0, 0.0, 100.0][: N - 1]
+    rho = [1000.0, 500.0, 100.0][: N - 1] + [1.0]
+    mu = [100.0, 50.0, 10.0][: N - 1] + [0.1]
+    x = np.arange(nx, dtype=np.float64)[None, :] + 0.5 - nx / 2.0
+    y = np.arange(ny, dtype=np.float64)[:, None] + 0.5 - ny / 2.0
+    phi = np.stack([0.5 + 0.5 * np.tanh((R - np.sqrt((x - c) ** 2 + y ** 2)) / (eps / 2.0))
+                    for c in centres])
+    for k in absent:
+        phi[k - 1] = 0.0
+    p = base_params(nx, ny, N, model=model, model_a_n=model_a_n, eps=eps, mobility=mobility,
+                    rho=rho, mu=mu, sigma=sigma)
+    return p, phi
+
+
 def compound_droplet(theta23, theta13=75.0, nx=300, ny=150, R=60.0, eps=5.0, sigma=0.01,
                      mobility=0.1, rho=(1.0, 0.5, 0.001), mu=(0.1, 0.05, 1e-4), model="B",
                      model_a_n=1.0):
