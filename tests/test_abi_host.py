@@ -79,6 +79,7 @@ def test_workspace_bytes_of_16bit_storage(lib):
     (dict(eps=float("nan")), 1), (dict(mobility=-0.1), 1), (dict(model="A", model_a_n=0.0), 1),
     (dict(gx=float("nan")), 1), (dict(storage=1, nx=63), 1), (dict(storage="f16", nx=65), 1),
     (dict(storage=7), 1),
+    (dict(nx=16384, ny=16385), 1), (dict(nx=(1 << 28) + 1, ny=1), 1),   # above 2^28 nodes
     (dict(wall_y=True, ny=3), 1),
     (dict(wall_cos=[0.5, 0.0, 0.0, 0.0]), 1),                 # wetting needs walls on y
     (dict(wall_y=True, wall_cos=[1.5, 0.0, 0.0, 0.0]), 1),   # |cos| <= 1
@@ -97,6 +98,19 @@ def test_parameter_validation(lib, mutate, status):
     with pytest.raises(nlbm.NlbmError) as ei:
         nlbm.nlbm_workspace_bytes(q)
     assert ei.value.status == status
+
+
+def test_largest_lattice_is_accepted(lib):
+    """2^28 nodes is the cap (plane offsets up to 8 planes stay in 32 bits);
+    its workspace is sized like any other lattice's."""
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.droplets_64("B")
+    small = nlbm.nlbm_workspace_bytes(p)
+    per_node = (nlbm.nlbm_workspace_bytes(dict(p, nx=128, ny=128)) - small) // (128 * 128 - 64 * 64)
+    fixed = small - per_node * 64 * 64
+    for nx, ny in [(16384, 16384), (1 << 28, 1), (1, 1 << 28)]:
+        big = nlbm.nlbm_workspace_bytes(dict(p, nx=nx, ny=ny))
+        assert abs(big - per_node * nx * ny - fixed) <= 4096
 
 
 def test_gravity_and_wetting_walls_are_accepted(lib):
