@@ -69,7 +69,7 @@ typedef enum { NLBM_STORE_F32 = 0, NLBM_STORE_BF16 = 1, NLBM_STORE_F16 = 2 } nlb
 
 /* The problem statement, in lattice units (dx = dt = 1, c_s^2 = 1/3). */
 typedef struct nlbm_params {
-    int32_t nx, ny;        /* lattice size, >= 1 each (>= 4 along a wall axis) */
+    int32_t nx, ny;        /* lattice size, >= 1 each (>= 4 along a wall axis), nx ny <= 2^28 */
     int32_t bc_x, bc_y;    /* nlbm_bc per axis */
     int32_t n_phases;      /* N, 2..8; phases 1..N-1 are solved, phase N is
                               1 - sum (Sec. 4) */
@@ -109,8 +109,8 @@ typedef struct nlbm_params {
 typedef struct nlbm_sim nlbm_sim;
 
 /* Bytes of device workspace one simulation with these parameters needs.
- * Validates the parameters (EINVAL / ENOTSUP as nlbm_create would).  Host
- * only, no GPU call. */
+ * Validates the parameters (EINVAL as nlbm_create would).  Host only, no
+ * GPU call. */
 nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes);
 
 /* Create a simulation.  dev_workspace: caller-owned device memory of at least
@@ -121,8 +121,8 @@ nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes);
  * later call is enqueued.  The parameters are copied; the caller may free
  * p->rho, p->mu, p->sigma afterwards.  The state is undefined until
  * nlbm_set_phi().  Errors: EINVAL (bad parameters, NULL pointers, unaligned
- * or too small workspace, odd nx with 16-bit storage), ENOTSUP (gravity),
- * ENOMEM (host handle allocation). */
+ * or too small workspace, odd nx with 16-bit storage, more than 2^28
+ * nodes), ENOMEM (host handle allocation). */
 nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t workspace_bytes,
                         void *cuda_stream, nlbm_sim **out);
 
