@@ -119,7 +119,7 @@ nlbm_status nlbm_workspace_bytes(const nlbm_params *p, size_t *bytes);
  * streaming), the auxiliary fields and reduction scratch in it.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
  * later call is enqueued.  The parameters are copied; the caller may free
- * p->rho, p->mu, p->sigma afterwards.  The state is undefined until
+ * p->rho, p->mu, p->sigma, p->wall_cos afterwards.  The state is undefined until
  * nlbm_set_phi().  Errors: EINVAL (bad parameters, NULL pointers, unaligned
  * or too small workspace, odd nx with 16-bit storage, more than 2^28
  * nodes), ENOMEM (host handle allocation). */
@@ -300,7 +300,7 @@ const char *nlbm_batch_last_error(const nlbm_batch *b);
  * Eqs. (16), (25); the Model B source, Eqs. (3)-(4); the stencils, Eq. (27);
  * streaming); states are checkpointed every `checkpoint_every` steps and
  * each segment is recomputed during the sweep.  Supported: Model B,
- * periodic on both axes, FP32 storage (ENOTSUP otherwise).  Unit vectors
+ * periodic on both axes, FP32 storage, no gravity (ENOTSUP otherwise).  Unit vectors
  * should use the smooth reading (p->unit_delta > 0, e.g. 1e-3): with the
  * thresholded one the step is not differentiable where v passes through 0.
  * ------------------------------------------------------------------------ */
