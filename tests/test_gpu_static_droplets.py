@@ -115,3 +115,36 @@ def test_table1_errors_16bit_storage(N, storage, rtol):
     np.testing.assert_allclose(e, want, rtol=rtol)
     assert umax < 5e-6
     assert np.all(np.abs(m1 - m0) <= 1e-6 * np.abs(m0))
+
+
+def test_table1_as_one_ensemble():
+    """The quaternary system under Model A (n = 1, 2) and Model B as the
+    three members of one ensemble (one persistent launch per step advances
+    all of them): each member gives the printed errors and, after 10,000
+    steps, the same bits as the simulation run alone (a member takes the
+    same code path), with its volumes conserved."""
+    import torch
+    from paper_2306_06983_gb300.nlbm import Batch
+    want = np.array(golden()[4])
+    members = [W.static_droplets(4, model=m, model_a_n=n) for m, n in MODELS]
+    b = Batch([p for p, _ in members])
+    for k, (_, phi0) in enumerate(members):
+        b.set_phi(k, phi0.astype(np.float32))
+    m0 = [b.phase_mass(k) for k in range(len(members))]
+    b.step(STEPS)
+    got = []
+    for k in range(len(members)):
+        phi, u, _ = (t.cpu().numpy().astype(np.float64) for t in b.moments(k))
+        got.append((np.concatenate([phi, (1.0 - phi.sum(0))[None]]), np.abs(u).max(), b.phase_mass(k)))
+    b.close()
+    torch.cuda.empty_cache()
+    for k, (model, n) in enumerate(MODELS):
+        full, umax, m1 = got[k]
+        alone, ana, _, _, _ = run(4, model, n)
+        e = np.array([rel_l1(full[j], ana[j]) for j in range(4)])
+        d = np.abs(full - alone).max()
+        print(f"\nensemble member {model} n={n}: E_L1 {' '.join(f'{v:.5e}' for v in e)}, "
+              f"max|u| {umax:.2e}, |member - alone| {d:.2e}")
+        np.testing.assert_allclose(e, want, rtol=5e-3)
+        assert umax < 1e-6 and d == 0.0
+        assert np.all(np.abs(m1 - m0[k]) <= 1e-6 * np.abs(m0[k]))
