@@ -213,7 +213,7 @@ def test_autograd_function_and_descent():
     with torch.no_grad():
         out2 = nphase_lbm(phi0, sig - step * sig.grad, mob, p, 200, 50)
         L2 = 0.5 * ((out2.double() - tgt.double()) ** 2).sum()
-    assert float(L2) < float(L)
+    assert float(L2) < float(L.detach())
 
 
 def test_taped_sweep_matches_tape_passes():
