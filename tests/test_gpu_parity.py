@@ -238,6 +238,26 @@ def test_transpose_symmetry_gpu():
     np.testing.assert_allclose(b[0][1][1], a[0][1][0].T, atol=max(1e-8, 2 * K * spread[1]))
 
 
+@pytest.mark.parametrize("model,n", [("B", 1.0), ("A", 2.0)])
+def test_phase_relabelling_symmetry_gpu(model, n):
+    """Relabelling the solved phases (densities, viscosities and tensions
+    permuted to match) relabels the result: 3 steps, within the FP32
+    spread.  The kernel's pair loops then run in another phase order."""
+    p, phi0 = W.random_smooth(64, 48, 4, seed=42, model=model, model_a_n=n)
+    phi0 = f32(phi0)
+    pi = [2, 0, 1, 3]
+    sig = np.asarray(p["sigma"])
+    q = dict(p, rho=[p["rho"][k] for k in pi], mu=[p["mu"][k] for k in pi],
+             sigma=sig[np.ix_(pi, pi)].tolist())
+    full0 = np.concatenate([phi0, (1.0 - phi0.sum(0))[None]])
+    _, a = gpu_run(p, phi0, 3)
+    _, b = gpu_run(q, np.ascontiguousarray(full0[pi][:3]), 3)
+    (_, spread, _), = fp32_spread(p, phi0, [3])
+    np.testing.assert_allclose(b[0][0], a[0][0][pi], atol=max(2e-6, 2 * K * spread[0]), rtol=0)
+    np.testing.assert_allclose(b[0][1], a[0][1], atol=max(1e-8, 2 * K * spread[1]), rtol=0)
+    np.testing.assert_allclose(b[0][2], a[0][2], atol=max(1e-8, 2 * K * spread[2]), rtol=0)
+
+
 def test_checkpoint_restore_bitwise():
     import torch
     from paper_2306_06983_gb300.nlbm import Simulation
