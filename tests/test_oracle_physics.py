@@ -139,16 +139,21 @@ def test_static_drop_matches_table1(oracle_built):
 
 def test_flat_interface_stationary(oracle_built):
     """Eq. (5): the flat profile 0.5 + 0.5 tanh(2x/eps) at rest is an
-    equilibrium; after 2000 steps it has moved by E_L1 < 5e-3 and drives no
-    flow (max |u| < 1e-6)."""
+    equilibrium of the continuum equations.  The lattice settles to its own
+    discrete profile, E_L1 = 1.78e-3 from the tanh at eps = 4 (below 2e-3).
+    That profile is stationary: from 2000 to 4000 steps it moves by
+    E_L1 = 2e-7 (bound 1e-6), and it drives no flow (max |u| < 1e-7)."""
     nx, ny = 16, 64
     p = W.base_params(nx, ny, 2, model="B", sigma=0.01)
     b = W.flat_band(nx, ny, 16, 48, 4.0)
     s = OracleSim(p, np.stack([b]))
     s.step(2000)
     phi, u, _ = s.moments()
-    assert np.abs(phi[0] - b).sum() / np.abs(b).sum() < 5e-3
-    assert np.abs(u).max() < 1e-6
+    assert np.abs(phi[0] - b).sum() / np.abs(b).sum() < 2e-3
+    assert np.abs(u).max() < 1e-7
+    s.step(2000)
+    phi2 = s.moments()[0]
+    assert np.abs(phi2[0] - phi[0]).sum() / np.abs(b).sum() < 1e-6
 
 
 @pytest.mark.parametrize("N", [2, 3])
