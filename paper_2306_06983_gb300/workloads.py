@@ -288,7 +288,7 @@ def static_droplets(N=4, model="B", model_a_n=1.0, absent=(), nx=300, ny=100, R=
 def compound_droplet(theta23, theta13=75.0, nx=300, ny=150, R=60.0, eps=5.0, sigma=0.01,
                      mobility=0.1, rho=(1.0, 0.5, 0.001), mu=(0.1, 0.05, 1e-4), model="B",
                      model_a_n=1.0):
-    """Compound droplet spreading on a solid wall (Sec. 4.2): a half-disk of
+    """Compound droplet on a wetting wall (Sec. 4.2): a half-disk of
     radius R on the bottom wall of [-nx/2, nx/2] x [0, ny], its left half
     phase 1 and its right half phase 2, in phase 3; periodic in x, the bottom
     wall wetting with contact angles theta13 and theta23 (degrees, against
