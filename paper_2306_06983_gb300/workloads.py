@@ -220,6 +220,25 @@ def lens(nx, ny, R, s12, s13, s23, model="B", model_a_n=1.0, eps=4.0, mobility=0
     return p, phi0
 
 
+def lens_papers_labels(nx, ny, R, s12, s23, s13=0.01, rho=(1.0, 0.5, 0.001), mu=(0.1, 0.05, 1e-4),
+                       model="B", model_a_n=1.0, eps=4.0, mobility=0.1):
+    """The liquid lens with the paper's labels and densities (Sec. 4.3):
+    phase 1 the lower layer, phase 2 the lens, phase 3 (the unsolved phase)
+    the upper layer; s12, s23 the lens's tensions against the lower and
+    upper layers, s13 the layers' own.  The printed densities and
+    viscosities are taken as lattice values (every kinematic viscosity
+    0.1); eps and the mobility are not given (4 and 0.1 here).  With a
+    density ratio of 1000 the light layer must be the unsolved phase: solved
+    as a phase set, it makes the run diverge.  Same geometry as lens()."""
+    p, phi0 = lens(nx, ny, R, s13, s12, s23, model=model, model_a_n=model_a_n, eps=eps,
+                   mobility=mobility)
+    full = np.concatenate([phi0, (1.0 - phi0.sum(0))[None]])
+    order = [0, 2, 1]          # lens() labels: 1 lower, 2 upper, 3 lens
+    sig = np.asarray(p["sigma"])[np.ix_(order, order)]
+    p = dict(p, rho=[float(v) for v in rho], mu=[float(v) for v in mu], sigma=sig.tolist())
+    return p, full[order][:2].copy()
+
+
 LENS_SIZES = ((128, 64), (256, 128), (512, 256))
 MODEL_A_SWEEP = (0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0)
 
