@@ -302,3 +302,27 @@ def test_lens_reaches_neumann_equilibrium(oracle_built):
     o.step(2000)
     _, hlo, hup, _ = measure_lens(o.moments()[0])
     assert hlo > 1.2 * hup
+
+
+def test_lens_at_density_ratio_1000_needs_the_light_phase_unsolved(oracle_built):
+    """The lens of Sec. 4.3 at the paper's densities (1 : 0.5 : 0.001 for
+    lower layer, lens, upper layer; every kinematic viscosity 0.1), equal
+    tensions, 160 x 64, R = 16.  With the paper's labels (the light upper
+    layer is the unsolved phase N) it settles after 10,000 steps. The cap
+    heights are then within 3% and the half-length within 6% of the
+    closed form.  The same problem with the lens as the unsolved phase (the
+    light layer solved as a phase set) diverges within 100 steps."""
+    from oracle.oracle import lens_equilibrium, measure_lens
+    p, phi0 = W.lens_papers_labels(160, 64, 16.0, 0.01, 0.01)
+    o = OracleSim(p, phi0)
+    o.step(10000)
+    phi = o.moments()[0]
+    assert np.isfinite(phi).all()
+    hd, hlo, hup, S = measure_lens(phi[[0, 2, 1]])
+    ad, alo, aup, _, _ = lens_equilibrium(0.01, 0.01, 0.01, S)
+    assert abs(hlo / alo - 1) < 0.03 and abs(hup / aup - 1) < 0.03, (hlo, hup, alo)
+    assert abs(hd / ad - 1) < 0.06, (hd, ad)
+    q, psi0 = W.lens(160, 64, 16.0, 0.01, 0.01, 0.01)
+    bad = OracleSim(dict(q, rho=[1.0, 0.001, 0.5], mu=[0.1, 1e-4, 0.05]), psi0)
+    bad.step(100)
+    assert not np.isfinite(bad.moments()[0]).all()
