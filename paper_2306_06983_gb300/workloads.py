@@ -207,7 +207,9 @@ def lens(nx, ny, R, s12, s13, s23, model="B", model_a_n=1.0, eps=4.0, mobility=0
     midway between the walls).  Periodic in x, no-flux walls at the bottom and
     top.  Profiles as in Sec. 4.3: the disk 0.5 + 0.5 tanh((R - r)/(eps/2)),
     the layers 0.5 + 0.5 tanh(2 (y0 - y)/eps) outside it.  Densities 1,
-    relaxation time 1 (mu = rho/6), mobility 0.1 unless given."""
+    relaxation time 1 (mu = rho/6), mobility 0.1 unless given.  For the
+    paper's 1000:500:1 densities use lens_papers_labels(): with the lens as
+    the unsolved phase and the light layer solved, that run diverges."""
     y0 = ny / 2.0 - 0.5 if y0 is None else float(y0)
     cx = nx / 2.0 - 0.5 if cx is None else float(cx)
     L = disk(nx, ny, cx, y0, R, eps, periodic_x=True, periodic_y=False)
