@@ -72,7 +72,10 @@ typedef struct nlbm_params {
     int32_t nx, ny;        /* lattice size, >= 1 each (>= 4 along a wall axis), nx ny <= 2^28 */
     int32_t bc_x, bc_y;    /* nlbm_bc per axis */
     int32_t n_phases;      /* N, 2..8; phases 1..N-1 are solved, phase N is
-                              1 - sum (Sec. 4) */
+                              1 - sum (Sec. 4).  At large density ratios make
+                              the lightest phase phase N: a three-phase lens
+                              at 1000:500:1 settles that way and diverges
+                              when the light phase is solved as a set */
     int32_t model;         /* nlbm_model */
     double model_a_n;      /* Model A exponent n > 0 (Eq. (2)); ignored by B */
     double eps;            /* interface thickness epsilon > 0 (Eq. (2)) */
