@@ -78,6 +78,7 @@ def _declare_sim(lib, real):
     lib.or_get_moments.argtypes = [ctypes.c_void_p, P(real), P(real), P(real)]
     lib.or_phase_mass.argtypes = [ctypes.c_void_p, P(real)]
     lib.or_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, P(real)]
+    lib.or_set_velocity.argtypes = [ctypes.c_void_p, P(real)]
     lib.or_steps_done.restype = ctypes.c_longlong
     lib.or_steps_done.argtypes = [ctypes.c_void_p]
     lib.or_max_threads.restype = ctypes.c_int
@@ -177,6 +178,17 @@ class OracleSim:
         assert phi0.shape == (self.N - 1, self.ny, self.nx), phi0.shape
         self.lib.or_set_phi(self.h, self._p(phi0))
 
+    def set_velocity(self, u0: np.ndarray):
+        """Start in motion: u0 [2, ny, nx] (or a pair (ux, uy) for a uniform
+        flow); populations at their equilibria, previous values equal to the
+        initial ones (see or_set_velocity)."""
+        u0 = np.asarray(u0, dtype=np.float64)
+        if u0.shape == (2,):
+            u0 = np.broadcast_to(u0[:, None, None], (2, self.ny, self.nx))
+        u0 = np.ascontiguousarray(u0, dtype=self._dt)
+        assert u0.shape == (2, self.ny, self.nx), u0.shape
+        self.lib.or_set_velocity(self.h, self._p(u0))
+
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
@@ -211,6 +223,7 @@ class OracleSim:
         which, shape = {
             "R": (0, (N, 2, ny, nx)), "mphi": (1, (2, ny, nx)), "muphi": (2, (N, ny, nx)),
             "F": (3, (2, ny, nx)), "grad": (4, (N, 2, ny, nx)), "lap": (5, (N, ny, nx)),
+            "Fc": (6, (2, ny, nx)),
         }[name]
         out = np.empty(shape, dtype=self._dt)
         self.lib.or_get_field(self.h, which, self._p(out))
