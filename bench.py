@@ -12,10 +12,13 @@ population buffers (604 MB each) are larger than L2, so no flush is needed.
 
 Beside the headline the line carries "forms": the same workload with
 bfloat16 / binary16 population storage (throughput, roofline fraction and
-distance to the FP32 fields after the same steps), the 64-member lens
-ensemble advanced in one persistent launch per step (against one launch per
-member), the ternary Rayleigh-Taylor instability (gravity and walls) and the
-differentiated run (forward and reverse sweep of the adjoint).
+distance to the FP32 fields after the same steps), the other model (Model A
+with n = 1 beside the Model B headline), the error of every storage against
+the FP64 oracle on the 256x256 cut of the workload (short and 2000-step
+horizons, both unit-vector readings), the 64-member lens ensemble advanced in
+one persistent launch per step (against one launch per member), the ternary
+Rayleigh-Taylor instability (gravity and walls) and the differentiated run
+(forward and reverse sweep of the adjoint).
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (weak scaling, no collective on the data path); rank 0 prints one
@@ -42,6 +45,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "N-phase LBM MLUPS & % HBM roofline: plain FP32 vs BF16/batched/adjoint forms"
 WORKLOAD = "2048x2048 periodic, N=5, 200 disks (seed 2306), eps=4, M=0.1"
+# GB300 HBM3e nominal bandwidth (GB/s); the roofline fraction is taken
+# against the measured copy bandwidth, this one is reported beside it
+NOMINAL_HBM_GBS = 8000.0
 
 
 def bytes_per_lup(N: int, storage: str = "f32") -> int:
@@ -254,12 +260,42 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
                 "value": round(lups / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
                 "algorithmic_bytes_per_lup": bpl,
                 "roofline_frac": round(bpl * lups / (ms / 1e3) / 1e9 / peak, 4),
+                # the minimum for 16-bit populations with every population
+                # (the rest one too) in 16 bits and N + 3 FP32 fields
+                "roofline_frac_at_min_bytes": round((44 * N + 20) * lups / (ms / 1e3) / 1e9 / peak, 4),
+                "min_bytes_per_lup": 44 * N + 20,
+                "of_f32_headline": None,
                 "vs_f32_after_same_steps": {
                     "steps": args.warmup + args.steps,
                     "max_abs_dphi": float(np.abs(phi - fphi).max()),
                     "u_rel_l2": float(np.sqrt(((u - fu) ** 2).sum() / max((fu ** 2).sum(), 1e-300)))},
                 "mass_drift_rel": float((np.abs(m1 - m0) / np.abs(m0)).max()),
             }
+
+        # the other model on the same workload (Model A with n = 1 beside the
+        # Model B headline, or B beside A), FP32
+        other = "A" if args.model == "B" else "B"
+        q, _ = W.disks_2048(other)
+        q = dict(q, storage="f32")
+        sim = Simulation(q, stream=stream)
+        sim.set_phi(phi0.astype(np.float32))
+        m0 = sim.phase_mass()
+        sim.step(args.warmup)
+        ms = timed(stream, sim.step, args.steps)
+        m1 = sim.phase_mass(allow_diverged=True)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        bpl = bytes_per_lup(N)
+        forms[f"model_{other}"] = {
+            "workload": WORKLOAD + f", Model {other}" + (" (n = 1)" if other == "A" else ""),
+            "value": round(lups / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
+            "algorithmic_bytes_per_lup": bpl,
+            "roofline_frac": round(bpl * lups / (ms / 1e3) / 1e9 / peak, 4),
+            "mass_drift_rel": float((np.abs(m1 - m0) / np.abs(m0)).max()),
+        }
+        if not args.no_oracle_accuracy:
+            forms["accuracy_256"] = measure_accuracy_256(args, stream)
 
         mem = W.lens_ensemble(64)
         nodes = sum(q["nx"] * q["ny"] for q, _ in mem)
@@ -301,6 +337,66 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         forms["rti"] = measure_rti(args, timed, stream, peak)
         forms["adjoint"] = measure_adjoint(timed)
     return forms
+
+
+def measure_accuracy_256(args, stream):
+    """Error of every population storage against the FP64 oracle on the
+    256x256 N = 5 cut of the workload (25 disks, radii U[6, 12], same
+    parameter draws, Model B): max |dphi| over all N phases, relative L2
+    error of u and the largest per-phase volume drift of the GPU run, after
+    a short horizon and after args.accuracy_steps steps, under both
+    unit-vector readings (delta = 0, the paper's v/|v| with 0 at v = 0, and
+    the smooth v/sqrt(|v|^2 + delta^2) with delta = 1e-3).  The oracle runs
+    on the host cores (OpenMP); the GPU runs are untimed."""
+    from oracle.oracle import OracleSim, build_oracle, max_threads
+    from paper_2306_06983_gb300 import workloads as W
+    from paper_2306_06983_gb300.nlbm import Simulation
+    build_oracle()
+    p, phi0 = W.disks_256(args.model)
+    phi0 = phi0.astype(np.float32).astype(np.float64)
+    horizons = (25, args.accuracy_steps)
+    out = {"workload": "256x256 periodic, N=5, 25 disks radii U[6, 12] (seed 2306), eps=4, M=0.1, "
+                       f"Model {args.model}; FP64 oracle on {max_threads()} host threads",
+           "steps": list(horizons), "readings": {}}
+    t0 = time.perf_counter()
+    for delta in (0.0, 1e-3):
+        q = dict(p, unit_delta=delta)
+        o = OracleSim(q, phi0)
+        ref = {}
+        done = 0
+        for h in horizons:
+            o.step(h - done)
+            done = h
+            ref[h] = o.moments()[:2]
+        res = {}
+        for st in ("f32", "bf16", "f16"):
+            with torch_stream(stream):
+                sim = Simulation(dict(q, storage=st), stream=stream)
+                sim.set_phi(phi0)
+                m0 = sim.phase_mass()
+                rows = {}
+                done = 0
+                for h in horizons:
+                    sim.step(h - done)
+                    done = h
+                    phi, u = (t.cpu().numpy().astype(np.float64) for t in sim.moments()[:2])
+                    m = sim.phase_mass(allow_diverged=True)
+                    ophi, ou = ref[h]
+                    rows[str(h)] = {
+                        "max_abs_dphi": float(np.abs(phi - ophi).max()),
+                        "u_rel_l2": float(np.sqrt(((u - ou) ** 2).sum() / max((ou ** 2).sum(), 1e-300))),
+                        "mass_drift_rel": float((np.abs(m - m0) / np.abs(m0)).max()),
+                    }
+                sim.close()
+            res[st] = rows
+        out["readings"][f"unit_delta={delta:g}"] = res
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
 
 
 def measure_rti(args, timed, stream, peak):
@@ -539,6 +635,8 @@ def run_gpu(args):
                      "kernel": f"step_kernel<NS={N - 1}, MODEL={args.model}, storage={args.storage}>",
                      "algorithmic_bytes_per_lup": bpl,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "nominal_peak": NOMINAL_HBM_GBS,
+                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "avg_launch_ms": round(avg_launch_s * 1e3, 5)},
         "e2e": {"value": round(whole_job_mlups(world, lups, args.steps, e2e_s), 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(4 * (N - 1) * lups / args.steps),
@@ -552,6 +650,10 @@ def run_gpu(args):
     }
     if not args.no_forms and world == 1:
         line["forms"] = measure_forms(args, p, phi0, ref_fields, lups, peak)
+        for st in ("bf16", "f16", "f32"):
+            f = line["forms"].get(st)
+            if f is not None and "of_f32_headline" in f:
+                f["of_f32_headline"] = round(f["value"] / line["value"], 4) if args.storage == "f32" else None
     if not args.no_cpu_baseline and world == 1:
         from oracle.oracle import build_oracle
         build_oracle()
@@ -580,6 +682,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=500,
                     help="oracle steps of the CPU baseline (about 10 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy-steps", type=int, default=2000,
+                    help="long horizon of the 256x256 comparison of every storage with the FP64 oracle")
+    ap.add_argument("--no-oracle-accuracy", action="store_true",
+                    help="skip the 256x256 comparison with the FP64 oracle among the forms")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the 16-bit storage and ensemble forms measured beside the headline")
     ap.add_argument("--only-forms", action="store_true",

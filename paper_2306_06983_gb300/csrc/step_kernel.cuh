@@ -1312,8 +1312,10 @@ cudaError_t launch_step_variant(const StepParams &p, int ty, int nslots, cudaStr
 // Row windows need nx a multiple of 4 (of 8 with 16-bit storage: rows and
 // planes start on 16-byte boundaries), 16-byte aligned arrays and no wall
 // across x (a wall bounces single columns back, which a window cannot
-// express); they are used unless their larger shared memory would leave
-// fewer blocks resident.
+// express); they are used whenever they apply, even where their larger
+// shared memory leaves fewer blocks resident (N = 7: two blocks per SM
+// with windows against three with per-node pulls, and the windows are
+// faster).
 template <int NS, int MODEL, int T, int ST, bool TAPE = false>
 cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
 {
@@ -1321,18 +1323,20 @@ cudaError_t launch_step_nst(const StepParams &p, int ty, cudaStream_t st)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    int plain = 0;
-    if ((e = variant_slots<NS, MODEL, T, ST, false, TAPE>(dev, &plain)) != cudaSuccess) return e;
     {
         uintptr_t a = reinterpret_cast<uintptr_t>(p.fin) | reinterpret_cast<uintptr_t>(p.gin);
         if (ST != 0)
             a |= reinterpret_cast<uintptr_t>(p.f0in) | reinterpret_cast<uintptr_t>(p.phi_prev) |
                  reinterpret_cast<uintptr_t>(p.pin);
         const bool vec = !p.wall_x && p.nx % (ST == 0 ? 4 : 8) == 0 && (a & 15) == 0;
-        int win = 0;
-        if (vec && (e = variant_slots<NS, MODEL, T, ST, true, TAPE>(dev, &win)) != cudaSuccess) return e;
-        if (vec && win >= plain) return launch_step_variant<NS, MODEL, T, ST, true, TAPE>(p, ty, win, st);
+        if (vec) {
+            int win = 0;
+            if ((e = variant_slots<NS, MODEL, T, ST, true, TAPE>(dev, &win)) != cudaSuccess) return e;
+            return launch_step_variant<NS, MODEL, T, ST, true, TAPE>(p, ty, win, st);
+        }
     }
+    int plain = 0;
+    if ((e = variant_slots<NS, MODEL, T, ST, false, TAPE>(dev, &plain)) != cudaSuccess) return e;
     return launch_step_variant<NS, MODEL, T, ST, false, TAPE>(p, ty, plain, st);
 }
 
