@@ -214,11 +214,17 @@ nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
  * larger sizes are rejected with NLBM_EINVAL (and one line on stderr)
  * before any GPU work.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress, with the device current); make it
- * before any stream capture.  All calls share the array: every entry the
- * reduction reads it has first written in the same call, so nothing needs
- * clearing, but calls that overlap on the GPU (other streams, other host
- * threads) race on it -- serialise them.  Asynchronous on cuda_stream
- * (a cudaStream_t, NULL = legacy default stream). */
+ * before any stream capture.  The address is cached per device together with
+ * the context it was taken in, and looked up again when a call runs in
+ * another context (a caller-created driver context, or the primary context
+ * re-created after cudaDeviceReset(), which discards the array's contents
+ * and may move it; after a reset the cached address is never reused unless
+ * the driver hands out the same context handle again, so make the first
+ * call after a reset outside stream capture too).  All calls share the array:
+ * every entry the reduction reads it has first written in the same call, so
+ * nothing needs clearing, but calls that overlap on the GPU (other streams,
+ * other host threads) race on it -- serialise them.  Asynchronous on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream). */
 nlbm_status nlbm_phase_mass_noalloc(const float *dev_phi, int32_t n_phases, int64_t n_nodes,
                                     double *dev_mass, int32_t *dev_flag, void *cuda_stream);
 

@@ -22,6 +22,29 @@ static __device__ __align__(256) double g_mass_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
+void *g_scratch_ctx[kMaxDevices] = {nullptr};   // context the address was looked up in
+
+// The current context of the calling thread (the driver's cuCtxGetCurrent,
+// reached through the runtime so that the library needs no link against
+// libcuda); nullptr if it cannot be obtained.
+void *current_context()
+{
+    typedef int (*get_ctx_fn)(void **);
+    static get_ctx_fn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<get_ctx_fn>(p);
+        looked_up = true;
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 // Rejections are reported by status code and one line on stderr (this entry
 // point has no handle to carry an error text).
@@ -38,7 +61,9 @@ void set_err(const char *fmt, ...)
 // Device address of the scratch array on the current device.  The host-side
 // name g_mass_scratch is only a stand-in; the address a kernel may use comes
 // from cudaGetSymbolAddress, looked up once per device with that device
-// current.
+// current, and again whenever the calling thread's current context differs
+// from the one the address was taken in (a caller's own driver context, or
+// the primary context re-created after cudaDeviceReset).
 nlbm_status scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -51,8 +76,11 @@ nlbm_status scratch_for_current_device(double **out)
         set_err("device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
         return NLBM_EINVAL;
     }
+    // (cudaGetDevice has made the device's primary context current if the
+    // thread had none, so the context read here is the one the kernels use)
+    void *ctx = current_context();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_mass_scratch);
         if (e != cudaSuccess || !p) {
@@ -60,6 +88,7 @@ nlbm_status scratch_for_current_device(double **out)
             return NLBM_ECUDA;
         }
         g_scratch_ptr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return NLBM_OK;

@@ -96,6 +96,61 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e)
     return s;
 }
 
+// Paired FP32 arithmetic.  Blackwell issues FADD2 / FMUL2 / FFMA2: one FP32
+// operation on two operand pairs in a single instruction, each component
+// rounded exactly as the scalar instruction (__fadd_rn, __fmul_rn,
+// __fmaf_rn).  The step is bound by instruction issue, so the work done per
+// phase runs on pairs of phases (p, p + 1) -- V = float2 -- and an odd last
+// phase on scalars, V = float, through the same code.
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+// a - b as the exact product -1 * b added to a with one rounding
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class V> __device__ __forceinline__ V vset(float s);
+template <> __device__ __forceinline__ float vset<float>(float s) { return s; }
+template <> __device__ __forceinline__ float2 vset<float2>(float s) { return make_float2(s, s); }
+// Phases p (and p + 1) of a per-phase array, and back.
+template <class V> __device__ __forceinline__ V vget(const float *a, int p);
+template <> __device__ __forceinline__ float vget<float>(const float *a, int p) { return a[p]; }
+template <> __device__ __forceinline__ float2 vget<float2>(const float *a, int p) { return make_float2(a[p], a[p + 1]); }
+__device__ __forceinline__ void vput(float *a, int p, float v) { a[p] = v; }
+__device__ __forceinline__ void vput(float *a, int p, float2 v) { a[p] = v.x; a[p + 1] = v.y; }
+// Values of phases p (and p + 1) at offset o of shared-memory rows that are
+// `stride` floats apart per phase.
+template <class V> __device__ __forceinline__ V vld(const float *base, int stride, int o);
+template <> __device__ __forceinline__ float vld<float>(const float *base, int, int o) { return base[o]; }
+template <> __device__ __forceinline__ float2 vld<float2>(const float *base, int stride, int o)
+{
+    return make_float2(base[o], base[stride + o]);
+}
+
+// phi = sum_i f_i in the fixed order f_0 + f_1 + ... + f_8 (own and halo
+// nodes give identical bits), and for the strip's own nodes the rounding
+// error of that sum (Fast2Sum terms, exact when the running sum dominates
+// each term, as the rest population does) and the first moments j.
+template <class V, bool OWN>
+__device__ __forceinline__ void pull_moments(const V (&f)[9], V &ph, V &plo, V &jx, V &jy)
+{
+    V s = f[0], e = vset<V>(0.f);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const V t = vadd(s, f[i]);
+        if (OWN) e = vadd(e, vsub(f[i], vsub(t, s)));
+        s = t;
+    }
+    ph = s;
+    if (OWN) {
+        plo = e;
+        jx = vadd(vadd(vsub(f[1], f[3]), vsub(f[5], f[6])), vsub(f[8], f[7]));
+        jy = vsub(vadd(vsub(f[2], f[4]), vadd(f[5], f[6])), vadd(f[7], f[8]));
+    }
+}
+
 // Asynchronous 4-byte global->shared copies (cp.async): the next row's
 // pulled populations are in flight while the current rows are computed.
 __device__ __forceinline__ void cp_async4(float *dst_smem, const float *src)
@@ -129,34 +184,27 @@ __device__ __forceinline__ void prefetch_pull(const StepParams &P, int x, int y,
     }
 }
 
-// Phase fields of one node from its staged pulled populations.  phi = f_0 +
-// f_1 + ... + f_8 is summed in this fixed order everywhere (own and halo
-// nodes give identical bits).  For the strip's own nodes the rounding error
-// of that sum (phi_lo, exact when the running sum dominates each term, as the
-// rest population does) and the first moments j_p are returned as well.
+// Phase fields of one node from its staged pulled populations (phases in
+// pairs, see pull_moments).
+template <class V, bool OWN>
+__device__ __forceinline__ void sum_pulled_v(const float *s_F, int WF, int col, int p, float *ph, float *plo,
+                                             float *jx, float *jy)
+{
+    V f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = vld<V>(s_F + (p * 9 + i) * WF, 9 * WF, col);
+    V a, lo, x, y;
+    pull_moments<V, OWN>(f, a, lo, x, y);
+    vput(ph, p, a);
+    if (OWN) { vput(plo, p, lo); vput(jx, p, x); vput(jy, p, y); }
+}
 template <int NS, bool OWN>
 __device__ __forceinline__ void sum_pulled(const float *s_F, int WF, int col, float (&ph)[NS],
                                            float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
 {
 #pragma unroll
-    for (int p = 0; p < NS; ++p) {
-        float f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = s_F[(p * 9 + i) * WF + col];
-        float s = f[0], e = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const float t = s + f[i];
-            if (OWN) e += f[i] - (t - s);     // Fast2Sum error term
-            s = t;
-        }
-        ph[p] = s;
-        if (OWN) {
-            plo[p] = e;
-            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        }
-    }
+    for (int p = 0; p + 1 < NS; p += 2) sum_pulled_v<float2, OWN>(s_F, WF, col, p, ph, plo, jx, jy);
+    if (NS & 1) sum_pulled_v<float, OWN>(s_F, WF, col, NS - 1, ph, plo, jx, jy);
 }
 
 // Row windows (FP32 storage, nx a multiple of 4, no wall across x).  Each
@@ -250,49 +298,130 @@ __device__ __forceinline__ WinCols win_cols(int b, bool bl, bool bh)
 }
 
 // sum_pulled from the warp's windows.
+template <class V, bool OWN>
+__device__ __forceinline__ void sum_pulled_win_v(const float *s_Fw, const WinCols &c, int p, float *ph,
+                                                 float *plo, float *jx, float *jy)
+{
+    const float *w = s_Fw + 9 * p * kWin;
+    constexpr int S = 9 * kWin;   // next phase
+    V f[9];
+    f[0] = vld<V>(w, S, c.b);
+    f[1] = vld<V>(w, S, kWin + c.b - 1);
+    f[2] = vld<V>(w, S, 2 * kWin + c.b);
+    f[3] = vld<V>(w, S, 3 * kWin + c.b + 1);
+    f[4] = vld<V>(w, S, 4 * kWin + c.b);
+    f[5] = vld<V>(w, S, 5 * kWin + c.c5);
+    f[6] = vld<V>(w, S, 6 * kWin + c.c6);
+    f[7] = vld<V>(w, S, 7 * kWin + c.c7);
+    f[8] = vld<V>(w, S, 8 * kWin + c.c8);
+    V a, lo, x, y;
+    pull_moments<V, OWN>(f, a, lo, x, y);
+    vput(ph, p, a);
+    if (OWN) { vput(plo, p, lo); vput(jx, p, x); vput(jy, p, y); }
+}
 template <int NS, bool OWN>
 __device__ __forceinline__ void sum_pulled_win(const float *s_Fw, const WinCols &c, float (&ph)[NS],
                                                float (&plo)[NS], float (&jx)[NS], float (&jy)[NS])
 {
 #pragma unroll
-    for (int p = 0; p < NS; ++p) {
-        const float *w = s_Fw + 9 * p * kWin;
-        float f[9];
-        f[0] = w[c.b];
-        f[1] = w[kWin + c.b - 1];
-        f[2] = w[2 * kWin + c.b];
-        f[3] = w[3 * kWin + c.b + 1];
-        f[4] = w[4 * kWin + c.b];
-        f[5] = w[5 * kWin + c.c5];
-        f[6] = w[6 * kWin + c.c6];
-        f[7] = w[7 * kWin + c.c7];
-        f[8] = w[8 * kWin + c.c8];
-        float s = f[0], e = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const float t = s + f[i];
-            if (OWN) e += f[i] - (t - s);
-            s = t;
-        }
-        ph[p] = s;
-        if (OWN) {
-            plo[p] = e;
-            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        }
+    for (int p = 0; p + 1 < NS; p += 2) sum_pulled_win_v<float2, OWN>(s_Fw, c, p, ph, plo, jx, jy);
+    if (NS & 1) sum_pulled_win_v<float, OWN>(s_Fw, c, NS - 1, ph, plo, jx, jy);
+}
+
+// Phase-field collision in moment space (Eqs. (18)-(20), (28)).  With the
+// relaxation rates of Sec. 4 (all 1 but s1 = 1/tau_f) the post-collision
+// moments of a phase set are phi, A = (1 - s1) j_x + s1 phi u_x + (1 - s1/2)
+// G_x / 3, B (the same along y), C = phi u_y / 3 + G_y / 18 and D = phi u_x / 3
+// + G_x / 18 (moments c_x^2 c_y and c_x c_y^2), the second moments phi / 3,
+// 0 and phi / 9 at equilibrium, with G = d_t(phi u) / c_s^2 + R_p the source
+// of Eq. (19).  The coefficients are the same for every phase.
+template <class V> struct CollCoef {
+    V s1, c1, h1, three, k18, ux, uy, mupx, mupy, s1ux, s1uy, ux3, uy3;
+    __device__ __forceinline__ CollCoef(float s1_, float ux_, float uy_, float upx_, float upy_)
+    {
+        s1 = vset<V>(s1_);
+        c1 = vset<V>(1.f - s1_);
+        h1 = vset<V>((1.f - 0.5f * s1_) * (1.f / 3.f));
+        three = vset<V>(3.f);
+        k18 = vset<V>(1.f / 18.f);
+        ux = vset<V>(ux_);
+        uy = vset<V>(uy_);
+        mupx = vset<V>(-upx_);
+        mupy = vset<V>(-upy_);
+        s1ux = vset<V>(s1_ * ux_);
+        s1uy = vset<V>(s1_ * uy_);
+        ux3 = vset<V>(ux_ * (1.f / 3.f));
+        uy3 = vset<V>(uy_ * (1.f / 3.f));
     }
+};
+
+template <class V>
+__device__ __forceinline__ void phase_moments(V phi, V jx, V jy, V php, V Rx, V Ry, const CollCoef<V> &k, V &A,
+                                              V &B, V &C, V &D)
+{
+    // G = d_t(phi u)/c_s^2 + R_p, backward Euler in time
+    const V Gx = vfma(k.three, vfma(php, k.mupx, vmul(phi, k.ux)), Rx);
+    const V Gy = vfma(k.three, vfma(php, k.mupy, vmul(phi, k.uy)), Ry);
+    A = vfma(k.c1, jx, vfma(phi, k.s1ux, vmul(k.h1, Gx)));
+    B = vfma(k.c1, jy, vfma(phi, k.s1uy, vmul(k.h1, Gy)));
+    C = vfma(phi, k.uy3, vmul(Gy, k.k18));
+    D = vfma(phi, k.ux3, vmul(Gx, k.k18));
+}
+
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float vcopysign(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ float2 vcopysign(float2 a, float2 b)
+{
+    return make_float2(copysignf(a.x, b.x), copysignf(a.y, b.y));
 }
 
 // Two populations c + h and c - h whose stored values sum to exactly 2c:
-// the larger is rounded, the smaller is 2c minus it (exact by Sterbenz's
-// lemma whenever |h| <= 3|c|, which holds away from vanishing phase fields).
-__device__ __forceinline__ void exact_pair(float c, float h, float &plus, float &minus)
+// big = c + |h| is rounded, and hr = big - c, c + hr = big and c - hr =
+// 2c - big are exact by Sterbenz's lemma whenever |h| <= 3|c|, which holds
+// away from vanishing phase fields; the sign of h picks which is which.
+template <class V>
+__device__ __forceinline__ void exact_pair_v(V c, V h, V &plus, V &minus)
 {
-    const float big = c + fabsf(h);
-    const float small = (c + c) - big;
-    plus = h >= 0.f ? big : small;
-    minus = h >= 0.f ? small : big;
+    const V big = vadd(c, vabs(h));
+    const V hr = vcopysign(vsub(big, c), h);
+    plus = vadd(c, hr);
+    minus = vsub(c, hr);
 }
+
+template <class V>
+__device__ __forceinline__ V two_sum_v(V a, V b, V &e)
+{
+    const V s = vadd(a, b);
+    const V bb = vsub(s, a);
+    e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+    return s;
+}
+
+// The nine post-collision populations f*_i = w_i phi + (moment terms) of
+// one or two phases from phi, the rounding error phi_lo of the pulled sum
+// and A, B, C, D.  The four +- pairs around phi/9 and phi/36 sum exactly to
+// 2 phi/9 or 2 phi/36, and f*_0 = 4 phi/9 is formed as (sum_i f_i) - 5 phi/9
+// with error-free subtractions, so the stored populations sum to the pulled
+// ones up to one rounding (volume conservation, Eq. (1)).
+template <class V>
+__device__ __forceinline__ void phase_populations(V phi, V plo, V A, V B, V C, V D, V (&f)[9])
+{
+    const V p9 = vmul(phi, vset<V>(1.f / 9.f)), p36 = vmul(vset<V>(0.25f), p9);
+    const V half = vset<V>(0.5f), quarter = vset<V>(0.25f);
+    exact_pair_v(p9, vmul(half, vsub(A, D)), f[1], f[3]);
+    exact_pair_v(p9, vmul(half, vsub(B, C)), f[2], f[4]);
+    exact_pair_v(p36, vmul(quarter, vadd(C, D)), f[5], f[7]);
+    exact_pair_v(p36, vmul(quarter, vsub(C, D)), f[6], f[8]);
+    V e1, e2;
+    const V a1 = two_sum_v(phi, vmul(vset<V>(-4.f), p9), e1);
+    const V a2 = two_sum_v(a1, vmul(vset<V>(-1.f), p9), e2);
+    f[0] = vadd(a2, vadd(vadd(e1, e2), plo));
+}
+
+// Store one value, or the values of phases p and p + 1 (`stride` floats apart).
+__device__ __forceinline__ void vstore(float *a, size_t, float v) { *a = v; }
+__device__ __forceinline__ void vstore(float *a, size_t stride, float2 v) { a[0] = v.x; a[stride] = v.y; }
 
 // 1/|v| of a unit vector: with the zero-gradient reading 0 when |v|^2 <=
 // 1e-24, or the smooth reading 1/sqrt(|v|^2 + delta^2) when delta2 > 0.
@@ -316,18 +445,58 @@ template <> struct Store16<2> {   // IEEE binary16, round to nearest even
     static __device__ __forceinline__ float dec(unsigned h) { return __half2float(__ushort_as_half((unsigned short)h)); }
 };
 
+// Two deviations in one 32-bit word (phase 2q in the low half, 2q + 1 in
+// the high half), converted together: one paired conversion rounds both to
+// nearest even, exactly as two calls of Store16::enc.
+template <int ST> struct Pack16;
+template <> struct Pack16<1> {
+    static __device__ __forceinline__ unsigned enc2(float2 v)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+    static __device__ __forceinline__ float2 dec2(unsigned w)
+    {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+};
+template <> struct Pack16<2> {
+    static __device__ __forceinline__ unsigned enc2(float2 v)
+    {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+    static __device__ __forceinline__ float2 dec2(unsigned w)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    }
+};
+
+// 16-bit deviation layout: phases 2q and 2q + 1 share one 32-bit word per
+// direction and node, [NS/2][8][plane] words; an odd last phase follows in
+// [8][plane] 16-bit planes.  i1 = direction - 1.
+__device__ __forceinline__ size_t dev_word(int q, int i1, unsigned pl, unsigned k)
+{
+    return ((size_t)q * 8 + i1) * pl + k;
+}
+__device__ __forceinline__ size_t dev_tail(int NS, int i1, unsigned pl, unsigned k)
+{
+    return (size_t)(NS / 2) * 16 * pl + (size_t)i1 * pl + k;   // in 16-bit units
+}
+
 // Lattice weights w_i (Sec. 4) as FP32 constants; the same constants are
 // used wherever a stored deviation is formed and wherever it is undone.
 __device__ __forceinline__ float w_of(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
 __device__ __forceinline__ int cx_of(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
 __device__ __forceinline__ int cy_of(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
 
-// Staging of the 16-bit populations a ring node pulls.  cp.async moves 4
-// bytes at least, so the aligned word holding each 16-bit value is copied
-// and the half is picked in stage A (par bit i: upper half for direction i;
-// nx is even, so every plane starts on a word boundary and the half is the
-// parity of the source node).  Slots per phase: 0 the FP32 rest population,
-// 1..8 the words of the moving deviations, 9 the puller's own phi(t).
+// Staging of the 16-bit populations a ring node pulls.  Slots per phase: 0
+// the FP32 rest population, 1..8 the moving deviations, 9 the puller's own
+// phi(t).  A phase pair's word is copied whole into the slots of its even
+// phase.  cp.async moves 4 bytes at least, so for an odd last phase the
+// aligned word holding each 16-bit value is copied and the half is picked in
+// stage A (par bit i: upper half for direction i; nx is even, so every plane
+// starts on a word boundary and the half is the parity of the source node).
 template <int NS>
 __device__ __forceinline__ unsigned prefetch_pull16(const StepParams &P, int x, int y, float *s_F,
                                                     int WF, int col)
@@ -336,6 +505,7 @@ __device__ __forceinline__ unsigned prefetch_pull16(const StepParams &P, int x, 
     int dir[9];
     pull_sources(P, x, y, node, dir);
     const unsigned pl = P.plane;
+    const unsigned *w32 = (const unsigned *)P.fin;
     const char *f16 = (const char *)P.fin;
     unsigned par = 0;
 #pragma unroll
@@ -343,12 +513,20 @@ __device__ __forceinline__ unsigned prefetch_pull16(const StepParams &P, int x, 
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
         cp_async4(s_F + (p * 10) * WF + col, P.f0in + (size_t)p * pl + node[0]);
+        cp_async4(s_F + (p * 10 + 9) * WF + col, P.phi_prev + (size_t)p * pl + node[0]);
+    }
+#pragma unroll
+    for (int q = 0; q < NS / 2; ++q) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            cp_async4(s_F + (2 * q * 10 + i) * WF + col, (const float *)(w32 + dev_word(q, dir[i] - 1, pl, node[i])));
+    }
+    if (NS & 1) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const size_t e = ((size_t)p * 8 + (unsigned)(dir[i] - 1)) * pl + node[i];
-            cp_async4(s_F + (p * 10 + i) * WF + col, (const float *)(f16 + ((e * 2) & ~(size_t)3)));
+            const size_t e = dev_tail(NS, dir[i] - 1, pl, node[i]);
+            cp_async4(s_F + ((NS - 1) * 10 + i) * WF + col, (const float *)(f16 + ((e * 2) & ~(size_t)3)));
         }
-        cp_async4(s_F + (p * 10 + 9) * WF + col, P.phi_prev + (size_t)p * pl + node[0]);
     }
     return par;
 }
@@ -361,7 +539,20 @@ __device__ __forceinline__ void sum_pulled16(const float *s_F, int WF, int col, 
                                              float (&jy)[NS])
 {
 #pragma unroll
-    for (int p = 0; p < NS; ++p) {
+    for (int p = 0; p + 1 < NS; p += 2) {
+        const float2 own = make_float2(s_F[(p * 10 + 9) * WF + col], s_F[((p + 1) * 10 + 9) * WF + col]);
+        float2 f[9];
+        f[0] = make_float2(s_F[(p * 10) * WF + col], s_F[((p + 1) * 10) * WF + col]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            f[i] = vfma(vset<float2>(w_of(i)), own, Pack16<ST>::dec2(__float_as_uint(s_F[(p * 10 + i) * WF + col])));
+        float2 a, lo, x, y;
+        pull_moments<float2, OWN>(f, a, lo, x, y);
+        vput(ph, p, a);
+        if (OWN) { vput(plo, p, lo); vput(jx, p, x); vput(jy, p, y); }
+    }
+    if (NS & 1) {
+        constexpr int p = NS - 1;
         const float own = s_F[(p * 10 + 9) * WF + col];
         float f[9];
         f[0] = s_F[(p * 10) * WF + col];
@@ -371,30 +562,23 @@ __device__ __forceinline__ void sum_pulled16(const float *s_F, int WF, int col, 
             const unsigned h = ((par >> i) & 1u) ? (wd >> 16) : (wd & 0xffffu);
             f[i] = __fmaf_rn(w_of(i), own, Store16<ST>::dec(h));
         }
-        float s = f[0], e = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const float t = s + f[i];
-            if (OWN) e += f[i] - (t - s);
-            s = t;
-        }
-        ph[p] = s;
-        if (OWN) {
-            plo[p] = e;
-            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        }
+        float a, lo, x, y;
+        pull_moments<float, OWN>(f, a, lo, x, y);
+        ph[p] = a;
+        if (OWN) { plo[p] = lo; jx[p] = x; jy[p] = y; }
     }
 }
 
 // Row windows of the 16-bit form (nx a multiple of 8, no wall across x).
-// Deviation planes: a window of kWin16 values (5 pieces of 8) starting at
-// the 8-aligned column ws at or left of the warp's first source column, so
-// lane l finds the value pulled along c_i at window column l + o16 - c_ix
-// (o16 = the warp's first node column - ws, 2 or 6).  FP32 planes read at the
-// node's own column (rest population, own phi) and the source pressure use
-// the kWin windows of the FP32 form.  Deviation pieces are copied by lanes
-// 0..29 (h = phase parity, group g, piece c), FP32 pieces by lanes 0..26.
+// Deviation planes: a window of kWin16 columns starting at the 8-aligned
+// column ws at or left of the warp's first source column, so lane l finds
+// the value pulled along c_i at window column l + o16 - c_ix (o16 = the
+// warp's first node column - ws, 2 or 6): per phase pair and direction 40
+// words (10 pieces of 16 bytes), for an odd last phase 40 16-bit values (5
+// pieces).  FP32 planes read at the node's own column (rest population, own
+// phi) and the source pressure use the kWin windows of the FP32 form.
+// Deviation pieces are copied by lanes 0..29 (group g, piece c), FP32 pieces
+// by lanes 0..26.
 constexpr int kWin16 = 40;
 
 __device__ __forceinline__ void cp_async16_raw(void *dst_smem, const void *src)
@@ -410,7 +594,8 @@ __device__ __forceinline__ unsigned wrap_col(int c, int nx)
 }
 
 // Copies of what node row y (ring row, image row under a y wall) pulls:
-// the deviation windows s_Dw [8 NS][kWin16] and the rest-population and
+// the deviation windows s_Dw (phase pairs [NS/2][8][kWin16] words, then an
+// odd last phase [8][kWin16] 16-bit values) and the rest-population and
 // own-phi windows s_Ow [2 NS][kWin] (rest populations first).
 template <int NS>
 __device__ __forceinline__ void stage_pull_rows16(const StepParams &P, int y, int lane, int ws, int xo,
@@ -418,20 +603,24 @@ __device__ __forceinline__ void stage_pull_rows16(const StepParams &P, int y, in
 {
     const unsigned pl = P.plane;
     if (lane < 30) {
-        const int h = lane / 15, g = (lane % 15) / 5, c = lane % 5;
+        const int g = lane / 10, c = lane % 10;
         int ge;
         unsigned row;
         group_source(P, y, g, ge, row);
-        const unsigned short *base = (const unsigned short *)P.fin + (row + wrap_col(ws + 8 * c, P.nx));
+        const unsigned *w32 = (const unsigned *)P.fin;
+        unsigned *dw = (unsigned *)s_Dw;
+        const unsigned col4 = row + wrap_col(ws + 4 * c, P.nx);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if (g == 0 && k == 0) continue;   // the rest population is FP32
-            const unsigned off = (unsigned)(group_dir(ge, k) - 1) * pl;
-            unsigned short *dst = s_Dw + (group_dir(g, k) - 1) * kWin16 + 8 * c;
+            const int i1 = group_dir(ge, k) - 1, d1 = group_dir(g, k) - 1;
 #pragma unroll
-            for (int m = 0; m < (NS + 1) / 2; ++m) {
-                const int p = h + 2 * m;
-                if (p < NS) cp_async16_raw(dst + 8 * p * kWin16, base + (size_t)p * 8 * pl + off);
+            for (int q = 0; q < NS / 2; ++q)
+                cp_async16_raw(dw + (q * 8 + d1) * kWin16 + 4 * c, w32 + dev_word(q, i1, pl, col4));
+            if ((NS & 1) && c < 5) {
+                const unsigned short *f16 = (const unsigned short *)P.fin;
+                cp_async16_raw(s_Dw + (NS / 2) * 16 * kWin16 + d1 * kWin16 + 8 * c,
+                               f16 + dev_tail(NS, i1, pl, row + wrap_col(ws + 8 * c, P.nx)));
             }
         }
     }
@@ -477,101 +666,152 @@ __device__ __forceinline__ void stage_flow_rows16(const StepParams &P, int y, in
     }
 }
 
-// sum_pulled16 from the warp's windows: f_i = w_i phi_own + dev_i.
+// sum_pulled16 from the warp's windows: f_i = w_i phi_own + dev_i (phases
+// in pairs, see pull_moments).
+template <class V, int NS, int ST, bool OWN>
+__device__ __forceinline__ void sum_pulled16_win_v(const unsigned short *s_Dw, const float *s_Ow, int lane,
+                                                   const WinCols &c, int p, float *ph, float *plo, float *jx,
+                                                   float *jy)
+{
+    const V own = vld<V>(s_Ow + (NS + p) * kWin, kWin, 2 + lane);
+    // the eight deviations: a phase pair's words, or an odd last phase's halves
+    auto dev = [&](int i1, int col) -> V {
+        if constexpr (sizeof(V) == 8) {
+            return Pack16<ST>::dec2(((const unsigned *)s_Dw)[((p / 2) * 8 + i1) * kWin16 + col]);
+        } else {
+            return Store16<ST>::dec(s_Dw[(NS / 2) * 16 * kWin16 + i1 * kWin16 + col]);
+        }
+    };
+    V f[9];
+    f[0] = vld<V>(s_Ow + p * kWin, kWin, 2 + lane);
+    f[1] = vfma(vset<V>(w_of(1)), own, dev(0, c.b - 1));
+    f[2] = vfma(vset<V>(w_of(2)), own, dev(1, c.b));
+    f[3] = vfma(vset<V>(w_of(3)), own, dev(2, c.b + 1));
+    f[4] = vfma(vset<V>(w_of(4)), own, dev(3, c.b));
+    f[5] = vfma(vset<V>(w_of(5)), own, dev(4, c.c5));
+    f[6] = vfma(vset<V>(w_of(6)), own, dev(5, c.c6));
+    f[7] = vfma(vset<V>(w_of(7)), own, dev(6, c.c7));
+    f[8] = vfma(vset<V>(w_of(8)), own, dev(7, c.c8));
+    V a, lo, x, y;
+    pull_moments<V, OWN>(f, a, lo, x, y);
+    vput(ph, p, a);
+    if (OWN) { vput(plo, p, lo); vput(jx, p, x); vput(jy, p, y); }
+}
 template <int NS, int ST, bool OWN>
 __device__ __forceinline__ void sum_pulled16_win(const unsigned short *s_Dw, const float *s_Ow, int lane,
                                                  const WinCols &c, float (&ph)[NS], float (&plo)[NS],
                                                  float (&jx)[NS], float (&jy)[NS])
 {
 #pragma unroll
-    for (int p = 0; p < NS; ++p) {
-        const float own = s_Ow[(NS + p) * kWin + 2 + lane];
-        const unsigned short *d = s_Dw + 8 * p * kWin16;
-        float f[9];
-        f[0] = s_Ow[p * kWin + 2 + lane];
-        f[1] = __fmaf_rn(w_of(1), own, Store16<ST>::dec(d[c.b - 1]));
-        f[2] = __fmaf_rn(w_of(2), own, Store16<ST>::dec(d[kWin16 + c.b]));
-        f[3] = __fmaf_rn(w_of(3), own, Store16<ST>::dec(d[2 * kWin16 + c.b + 1]));
-        f[4] = __fmaf_rn(w_of(4), own, Store16<ST>::dec(d[3 * kWin16 + c.b]));
-        f[5] = __fmaf_rn(w_of(5), own, Store16<ST>::dec(d[4 * kWin16 + c.c5]));
-        f[6] = __fmaf_rn(w_of(6), own, Store16<ST>::dec(d[5 * kWin16 + c.c6]));
-        f[7] = __fmaf_rn(w_of(7), own, Store16<ST>::dec(d[6 * kWin16 + c.c7]));
-        f[8] = __fmaf_rn(w_of(8), own, Store16<ST>::dec(d[7 * kWin16 + c.c8]));
-        float s = f[0], e = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const float t = s + f[i];
-            if (OWN) e += f[i] - (t - s);
-            s = t;
-        }
-        ph[p] = s;
-        if (OWN) {
-            plo[p] = e;
-            jx[p] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            jy[p] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        }
+    for (int p = 0; p + 1 < NS; p += 2)
+        sum_pulled16_win_v<float2, NS, ST, OWN>(s_Dw, s_Ow, lane, c, p, ph, plo, jx, jy);
+    if (NS & 1) sum_pulled16_win_v<float, NS, ST, OWN>(s_Dw, s_Ow, lane, c, NS - 1, ph, plo, jx, jy);
+}
+
+// Eq. (27) on a 3x3 window (rows south, centre, north): the isotropic
+// central gradient and, with LAP, the Laplacian, for one or two phases.
+template <class V, bool LAP>
+__device__ __forceinline__ void grad_lap9(V sw, V s, V se, V w, V ce, V e, V nw, V n, V ne, V &gx, V &gy,
+                                          V &lap)
+{
+    const V k3 = vset<V>(1.f / 3.f), k12 = vset<V>(1.f / 12.f);
+    gx = vfma(vsub(e, w), k3, vmul(vsub(vadd(ne, se), vadd(nw, sw)), k12));
+    gy = vfma(vsub(n, s), k3, vmul(vsub(vadd(ne, nw), vadd(se, sw)), k12));
+    if (LAP) {
+        const V ax = vadd(vadd(vsub(e, ce), vsub(w, ce)), vadd(vsub(n, ce), vsub(s, ce)));
+        const V dg = vadd(vadd(vsub(ne, ce), vsub(nw, ce)), vadd(vsub(se, ce), vsub(sw, ce)));
+        lap = vfma(ax, vset<V>(2.f / 3.f), vmul(dg, vset<V>(1.f / 6.f)));
     }
 }
 
-// 3x3 window of the phase fields in the ring: phi, grad phi (Eq. (27)) for
-// all N phases (phase N by phi_N = 1 - sum, grad phi_N = -sum).
+// Phases p (and p + 1) of the 3x3 window of the phi ring at column c.
+template <class V, bool LAP>
+__device__ __forceinline__ void window_v(const float *s_phi, int W, int NS, int sm, int s0, int sp, int c, int p,
+                                         V &ce, V &gx, V &gy, V &lap)
+{
+    const float *rm = s_phi + (sm * NS + p) * W + c;
+    const float *r0 = s_phi + (s0 * NS + p) * W + c;
+    const float *rp = s_phi + (sp * NS + p) * W + c;
+    ce = vld<V>(r0, W, 0);
+    grad_lap9<V, LAP>(vld<V>(rm, W, -1), vld<V>(rm, W, 0), vld<V>(rm, W, 1), vld<V>(r0, W, -1), ce,
+                      vld<V>(r0, W, 1), vld<V>(rp, W, -1), vld<V>(rp, W, 0), vld<V>(rp, W, 1), gx, gy, lap);
+}
+
+// phi, grad phi (Eq. (27)) and, with LAP, lap phi of all N phases from one
+// read of the 3x3 window of the ring (phase N by phi_N = 1 - sum and
+// negated sums).
+template <int NS, bool LAP>
+__device__ __forceinline__ void window_fields(const float *s_phi, int W, int sm, int s0, int sp, int c,
+                                              float (&ph)[NS + 1], float (&gx)[NS + 1], float (&gy)[NS + 1],
+                                              float (&lap)[NS + 1])
+{
+    float2 sph = make_float2(0.f, 0.f), sgx = sph, sgy = sph, sl = sph;
+#pragma unroll
+    for (int p = 0; p + 1 < NS; p += 2) {
+        float2 a, x, y, l;
+        window_v<float2, LAP>(s_phi, W, NS, sm, s0, sp, c, p, a, x, y, l);
+        vput(ph, p, a);
+        vput(gx, p, x);
+        vput(gy, p, y);
+        sph = vadd(sph, a);
+        sgx = vadd(sgx, x);
+        sgy = vadd(sgy, y);
+        if (LAP) { vput(lap, p, l); sl = vadd(sl, l); }
+    }
+    float tph = sph.x + sph.y, tgx = sgx.x + sgx.y, tgy = sgy.x + sgy.y, tl = sl.x + sl.y;
+    if (NS & 1) {
+        float a, x, y, l;
+        window_v<float, LAP>(s_phi, W, NS, sm, s0, sp, c, NS - 1, a, x, y, l);
+        ph[NS - 1] = a;
+        gx[NS - 1] = x;
+        gy[NS - 1] = y;
+        tph += a;
+        tgx += x;
+        tgy += y;
+        if (LAP) { lap[NS - 1] = l; tl += l; }
+    }
+    ph[NS] = 1.f - tph;
+    gx[NS] = -tgx;
+    gy[NS] = -tgy;
+    if (LAP) lap[NS] = -tl;
+}
+
 template <int NS>
 __device__ __forceinline__ void window_grad(const float *s_phi, int W, int sm, int s0, int sp,
                                             int c, float (&ph)[NS + 1], float (&gx)[NS + 1],
                                             float (&gy)[NS + 1])
 {
-    float sph = 0.f, sgx = 0.f, sgy = 0.f;
-#pragma unroll
-    for (int p = 0; p < NS; ++p) {
-        const float *rm = s_phi + (sm * NS + p) * W + c;
-        const float *r0 = s_phi + (s0 * NS + p) * W + c;
-        const float *rp = s_phi + (sp * NS + p) * W + c;
-        const float sw = rm[-1], s = rm[0], se = rm[1];
-        const float w = r0[-1], ce = r0[0], e = r0[1];
-        const float nw = rp[-1], n = rp[0], ne = rp[1];
-        ph[p] = ce;
-        gx[p] = (e - w) * (1.f / 3.f) + ((ne + se) - (nw + sw)) * (1.f / 12.f);
-        gy[p] = (n - s) * (1.f / 3.f) + ((ne + nw) - (se + sw)) * (1.f / 12.f);
-        sph += ce;
-        sgx += gx[p];
-        sgy += gy[p];
-    }
-    ph[NS] = 1.f - sph;
-    gx[NS] = -sgx;
-    gy[NS] = -sgy;
+    float lap[NS + 1];
+    window_fields<NS, false>(s_phi, W, sm, s0, sp, c, ph, gx, gy, lap);
 }
 
-// phi, grad phi and lap phi (Eq. (27)) of all N phases from one read of the
-// 3x3 window (phase N by phi_N = 1 - sum and negated sums).
 template <int NS>
 __device__ __forceinline__ void window_grad_lap(const float *s_phi, int W, int sm, int s0, int sp,
                                                 int c, float (&ph)[NS + 1], float (&gx)[NS + 1],
                                                 float (&gy)[NS + 1], float (&lap)[NS + 1])
 {
-    float sph = 0.f, sgx = 0.f, sgy = 0.f, sl = 0.f;
-#pragma unroll
-    for (int p = 0; p < NS; ++p) {
-        const float *rm = s_phi + (sm * NS + p) * W + c;
-        const float *r0 = s_phi + (s0 * NS + p) * W + c;
-        const float *rp = s_phi + (sp * NS + p) * W + c;
-        const float sw = rm[-1], s = rm[0], se = rm[1];
-        const float w = r0[-1], ce = r0[0], e = r0[1];
-        const float nw = rp[-1], n = rp[0], ne = rp[1];
-        ph[p] = ce;
-        gx[p] = (e - w) * (1.f / 3.f) + ((ne + se) - (nw + sw)) * (1.f / 12.f);
-        gy[p] = (n - s) * (1.f / 3.f) + ((ne + nw) - (se + sw)) * (1.f / 12.f);
-        const float ax = ((e - ce) + (w - ce)) + ((n - ce) + (s - ce));
-        const float dg = ((ne - ce) + (nw - ce)) + ((se - ce) + (sw - ce));
-        lap[p] = ax * (2.f / 3.f) + dg * (1.f / 6.f);
-        sph += ce;
-        sgx += gx[p];
-        sgy += gy[p];
-        sl += lap[p];
+    window_fields<NS, true>(s_phi, W, sm, s0, sp, c, ph, gx, gy, lap);
+}
+
+// 1/|v| from |v|^2, as inv_norm.
+__device__ __forceinline__ float inv_norm2(float n2, float delta2)
+{
+    if (delta2 > 0.f) return rsqrtf(n2 + delta2);
+    return n2 > 1e-24f ? rsqrtf(n2) : 0.0f;
+}
+
+// Model A weight max(phi, 0)^n (integer n by multiplication).
+__device__ __forceinline__ float model_a_weight(const StepParams &P, float ph)
+{
+    const float pc = fmaxf(ph, 0.f);
+    if (P.model_n_int == 1) return pc;
+    if (P.model_n_int == 2) return pc * pc;
+    if (P.model_n_int > 2) {
+        float wq = pc;
+        for (int k = 1; k < P.model_n_int; ++k) wq *= pc;
+        return wq;
     }
-    ph[NS] = 1.f - sph;
-    gx[NS] = -sgx;
-    gy[NS] = -sgy;
-    lap[NS] = -sl;
+    return powf(pc, P.model_n);
 }
 
 // Source R_p of the solved phases (Eqs. (2)-(4)).
@@ -583,47 +823,83 @@ __device__ __forceinline__ void source_terms(const StepParams &P, const float (&
     constexpr int N = NS + 1;
     if (MODEL == 0) {
         // Model A, Eq. (2): R_p = a_p n_p - phi_p^n / sum_q phi_q^n * sum_q a_q n_q
-        float a[N], nxv[N], nyv[N], w[N];
-        float S = 0.f, Vx = 0.f, Vy = 0.f;
+        float anx[N], any[N], w[N];
+        float2 S2 = make_float2(0.f, 0.f), V2x = S2, V2y = S2;
 #pragma unroll
-        for (int q = 0; q < N; ++q) {
-            a[q] = P.four_over_eps * ph[q] * (1.f - ph[q]);
-            const float r = inv_norm(gx[q], gy[q], P.unit_delta2);
-            nxv[q] = gx[q] * r;
-            nyv[q] = gy[q] * r;
-            const float pc = fmaxf(ph[q], 0.f);
-            float wq;
-            if (P.model_n_int == 1) {
-                wq = pc;
-            } else if (P.model_n_int == 2) {
-                wq = pc * pc;
-            } else if (P.model_n_int > 2) {
-                wq = pc;
-                for (int k = 1; k < P.model_n_int; ++k) wq *= pc;
-            } else {
-                wq = powf(pc, P.model_n);
-            }
-            w[q] = wq;
-            S += wq;
-            Vx += a[q] * nxv[q];
-            Vy += a[q] * nyv[q];
+        for (int q = 0; q + 1 < N; q += 2) {
+            const float2 f = vget<float2>(ph, q);
+            const float2 a = vmul(vmul(vset<float2>(P.four_over_eps), f), vsub(vset<float2>(1.f), f));
+            const float2 r = make_float2(inv_norm(gx[q], gy[q], P.unit_delta2), inv_norm(gx[q + 1], gy[q + 1], P.unit_delta2));
+            const float2 ar = vmul(a, r);
+            const float2 nx2 = vmul(ar, vget<float2>(gx, q)), ny2 = vmul(ar, vget<float2>(gy, q));
+            vput(anx, q, nx2);
+            vput(any, q, ny2);
+            const float2 wq = make_float2(model_a_weight(P, f.x), model_a_weight(P, f.y));
+            vput(w, q, wq);
+            S2 = vadd(S2, wq);
+            V2x = vadd(V2x, nx2);
+            V2y = vadd(V2y, ny2);
+        }
+        float S = S2.x + S2.y, Vx = V2x.x + V2x.y, Vy = V2y.x + V2y.y;
+        if (N & 1) {
+            const int q = N - 1;
+            const float a = P.four_over_eps * ph[q] * (1.f - ph[q]);
+            const float ar = a * inv_norm(gx[q], gy[q], P.unit_delta2);
+            anx[q] = ar * gx[q];
+            any[q] = ar * gy[q];
+            w[q] = model_a_weight(P, ph[q]);
+            S += w[q];
+            Vx += anx[q];
+            Vy += any[q];
         }
         const float invS = 1.f / S;
+        const float2 Vx2 = vset<float2>(Vx), Vy2 = vset<float2>(Vy), iS2 = vset<float2>(-invS);
 #pragma unroll
-        for (int p = 0; p < NS; ++p) {
-            const float b = w[p] * invS;
-            Rx[p] = a[p] * nxv[p] - b * Vx;
-            Ry[p] = a[p] * nyv[p] - b * Vy;
+        for (int p = 0; p + 1 < NS; p += 2) {
+            const float2 b = vmul(vget<float2>(w, p), iS2);   // -beta weight
+            vput(Rx, p, vfma(b, Vx2, vget<float2>(anx, p)));
+            vput(Ry, p, vfma(b, Vy2, vget<float2>(any, p)));
+        }
+        if (NS & 1) {
+            const float b = w[NS - 1] * invS;
+            Rx[NS - 1] = anx[NS - 1] - b * Vx;
+            Ry[NS - 1] = any[NS - 1] - b * Vy;
         }
     } else {
         // Model B, Eqs. (3)-(4): R_p = sum_{q!=p} 4 phi_p phi_q / eps n_pq,
         // n_pq = unit(phi_q grad phi_p - phi_p grad phi_q), n_qp = -n_pq.
+        // The partners q of phase p are taken two at a time.
 #pragma unroll
         for (int p = 0; p < NS; ++p) { Rx[p] = 0.f; Ry[p] = 0.f; }
 #pragma unroll
         for (int p = 0; p < N; ++p) {
+            const float2 kp = vset<float2>(-(P.four_over_eps * ph[p]));
+            const float2 gxp = vset<float2>(gx[p]), gyp = vset<float2>(gy[p]), mp = vset<float2>(-ph[p]);
+            int q = p + 1;
 #pragma unroll
-            for (int q = p + 1; q < N; ++q) {
+            for (; q + 1 < N; q += 2) {
+                const float2 phq = vget<float2>(ph, q);
+                const float2 vx = vfma(phq, gxp, vmul(mp, vget<float2>(gx, q)));
+                const float2 vy = vfma(phq, gyp, vmul(mp, vget<float2>(gy, q)));
+                const float2 n2 = vfma(vx, vx, vmul(vy, vy));
+                // cn = -4 phi_p phi_q / eps / |v|
+                const float2 cn = vmul(vmul(kp, phq), make_float2(inv_norm2(n2.x, P.unit_delta2),
+                                                                  inv_norm2(n2.y, P.unit_delta2)));
+                if (p < NS) {
+                    Rx[p] = __fmaf_rn(-cn.x, vx.x, Rx[p]);
+                    Ry[p] = __fmaf_rn(-cn.x, vy.x, Ry[p]);
+                    Rx[p] = __fmaf_rn(-cn.y, vx.y, Rx[p]);
+                    Ry[p] = __fmaf_rn(-cn.y, vy.y, Ry[p]);
+                }
+                if (q + 1 < NS) {
+                    vput(Rx, q, vfma(cn, vx, vget<float2>(Rx, q)));
+                    vput(Ry, q, vfma(cn, vy, vget<float2>(Ry, q)));
+                } else if (q < NS) {
+                    Rx[q] = __fmaf_rn(cn.x, vx.x, Rx[q]);
+                    Ry[q] = __fmaf_rn(cn.x, vy.x, Ry[q]);
+                }
+            }
+            if (q < N) {
                 const float vx = ph[q] * gx[p] - ph[p] * gx[q];
                 const float vy = ph[q] * gy[p] - ph[p] * gy[q];
                 const float c = P.four_over_eps * ph[p] * ph[q] * inv_norm(vx, vy, P.unit_delta2);
@@ -938,22 +1214,45 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                 gry += P.drho[p] * gy[p];
             }
 
-            // chemical potentials (Eq. (17)) and F_s = sum_p mu_p grad phi_p (Eq. (16))
+            // chemical potentials (Eq. (17)) and F_s = sum_p mu_p grad phi_p
+            // (Eq. (16)); the partners q of phase p two at a time
             float gp[N], muph[N];
+            {
+                const float2 one = vset<float2>(1.f), two = vset<float2>(2.f);
 #pragma unroll
-            for (int p = 0; p < N; ++p) {
-                gp[p] = 2.f * ph[p] * (1.f - ph[p]) * (1.f - 2.f * ph[p]);
-                muph[p] = 0.f;
-            }
+                for (int p = 0; p + 1 < N; p += 2) {
+                    const float2 f = vget<float2>(ph, p);
+                    vput(gp, p, vmul(vmul(vmul(two, f), vsub(one, f)), vfma(vset<float2>(-2.f), f, one)));
+                }
+                if (N & 1) gp[N - 1] = 2.f * ph[N - 1] * (1.f - ph[N - 1]) * (1.f - 2.f * ph[N - 1]);
 #pragma unroll
-            for (int p = 0; p < N; ++p) {
+                for (int p = 0; p < N; ++p) muph[p] = 0.f;
 #pragma unroll
-                for (int q = p + 1; q < N; ++q) {
-                    const float s = ph[p] + ph[q];
-                    const float G = 2.f * s * (1.f - s) * (1.f - 2.f * s);
-                    const float b = P.beta2[p][q], k = P.kap[p][q];
-                    muph[p] += b * (gp[p] - G) + k * lap[q];
-                    muph[q] += b * (gp[q] - G) + k * lap[p];
+                for (int p = 0; p < N; ++p) {
+                    const float2 php2 = vset<float2>(ph[p]), gpp = vset<float2>(gp[p]), lpp = vset<float2>(lap[p]);
+                    int q = p + 1;
+#pragma unroll
+                    for (; q + 1 < N; q += 2) {
+                        const float2 sq = vadd(php2, vget<float2>(ph, q));
+                        const float2 G = vmul(vmul(vmul(two, sq), vsub(one, sq)), vfma(vset<float2>(-2.f), sq, one));
+                        const float2 b = make_float2(P.beta2[p][q], P.beta2[p][q + 1]);
+                        const float2 k = make_float2(P.kap[p][q], P.kap[p][q + 1]);
+                        // mu_p accumulates its terms in the order q, q + 1
+                        // (the pairwise sum keeps the cancellation of
+                        // g'(phi_p) - g'(phi_p + phi_q) where phase q is
+                        // nearly absent; the adjoint's gradients depend on it)
+                        const float2 tp = vfma(b, vsub(gpp, G), vmul(k, vget<float2>(lap, q)));
+                        muph[p] += tp.x;
+                        muph[p] += tp.y;
+                        vput(muph, q, vadd(vget<float2>(muph, q), vfma(b, vsub(vget<float2>(gp, q), G), vmul(k, lpp))));
+                    }
+                    if (q < N) {
+                        const float sq = ph[p] + ph[q];
+                        const float G = 2.f * sq * (1.f - sq) * (1.f - 2.f * sq);
+                        const float b = P.beta2[p][q], k = P.kap[p][q];
+                        muph[p] += b * (gp[p] - G) + k * lap[q];
+                        muph[q] += b * (gp[q] - G) + k * lap[p];
+                    }
                 }
             }
             float Fx = 0.f, Fy = 0.f;
@@ -1031,11 +1330,13 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             const float Pyy = (g[2] + g[4]) + d58;
             const float Pxy = (g[5] - g[6]) + (g[7] - g[8]);
             const float inv_rho = 1.f / rho;
-            const float ux = (jgx + 0.5f * Fx) * inv_rho;
-            const float uy = (jgy + 0.5f * Fy) * inv_rho;
+            const float2 uv = vmul(vfma(vset<float2>(0.5f), make_float2(Fx, Fy), make_float2(jgx, jgy)),
+                                   vset<float2>(inv_rho));
+            const float ux = uv.x, uy = uv.y;
             const float mphx = Mcx, mphy = Mcy;
             const float upx = Ucx, upy = Ucy;
-            const float mx = rho * ux + mphx, my = rho * uy + mphy;
+            const float2 mv = vfma(vset<float2>(rho), uv, make_float2(mphx, mphy));
+            const float mx = mv.x, my = mv.y;
             const float ugr = ux * grx + uy * gry;
             float rho_prev = P.rhoN;
 #pragma unroll
@@ -1057,100 +1358,87 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                        (cy_of(j) > 0 && byh);
             };
             (void)bounce;
-            const float s1 = P.s1, c1 = 1.f - s1, h1 = (1.f - 0.5f * s1) * (1.f / 3.f);
-#pragma unroll
-            for (int p = 0; p < NS; ++p) {
-                const float phi = ph[p];
-                const float jx = s_j[(s3 * 3 * NS + 3 * p) * T + t];
-                const float jy = s_j[(s3 * 3 * NS + 3 * p + 1) * T + t];
-                const float plo = s_j[(s3 * 3 * NS + 3 * p + 2) * T + t];
-                const float Rx = Rcx[p], Ry = Rcy[p];
-                // G = d_t(phi u)/c_s^2 + R_p
-                const float Gx = 3.f * (phi * ux - php[p] * upx) + Rx;
-                const float Gy = 3.f * (phi * uy - php[p] * upy) + Ry;
-                const float A = c1 * jx + s1 * phi * ux + h1 * Gx;
-                const float B = c1 * jy + s1 * phi * uy + h1 * Gy;
-                const float C = phi * uy * (1.f / 3.f) + Gy * (1.f / 18.f);
-                const float D = phi * ux * (1.f / 3.f) + Gx * (1.f / 18.f);
-                // f*_i = w_i phi + (moment terms); the four +-pairs around
-                // phi/9 and phi/36 are stored so that each sums exactly to
-                // 2 phi/9 or 2 phi/36, and f*_0 = 4 phi/9 is formed as
-                // (sum_i f_i) - 5 p9 with error-free subtractions, so the
-                // stored populations sum to the pulled ones up to one
-                // rounding (volume conservation, Eq. (1)).
+            const CollCoef<float2> k2(P.s1, ux, uy, upx, upy);
+            const CollCoef<float> k1(P.s1, ux, uy, upx, upy);
+            const float *sj = s_j + (s3 * 3 * NS) * T + t;   // j_x, j_y, phi_lo of phase p at sj + 3 p T
+            auto collide = [&](auto tag, const auto &k, int p) {
+                using V = decltype(tag);
+                V A, B, C, D;
+                phase_moments<V>(vget<V>(ph, p), vld<V>(sj, 3 * T, 3 * p * T), vld<V>(sj, 3 * T, (3 * p + 1) * T),
+                                 vget<V>(php, p), vget<V>(Rcx, p), vget<V>(Rcy, p), k, A, B, C, D);
                 if constexpr (ST == 0) {
-                    const float p9 = phi * (1.f / 9.f), p36 = 0.25f * p9;
-                    float f1, f2, f3, f4, f5, f6, f7, f8;
-                    exact_pair(p9, 0.5f * (A - D), f1, f3);
-                    exact_pair(p9, 0.5f * (B - C), f2, f4);
-                    exact_pair(p36, 0.25f * (C + D), f5, f7);
-                    exact_pair(p36, 0.25f * (C - D), f6, f8);
-                    float e1, e2;
-                    const float a1 = two_sum(phi, -4.f * p9, e1);
-                    const float a2 = two_sum(a1, -p9, e2);
-                    const float f0 = a2 + ((e1 + e2) + plo);
-                    float *fo = P.fout + (size_t)p * 9 * pl + node;
-                    fo[0 * pl] = f0;
-                    fo[1 * pl] = f1;
-                    fo[2 * pl] = f2;
-                    fo[3 * pl] = f3;
-                    fo[4 * pl] = f4;
-                    fo[5 * pl] = f5;
-                    fo[6 * pl] = f6;
-                    fo[7 * pl] = f7;
-                    fo[8 * pl] = f8;
+                    V fo[9];
+                    phase_populations<V>(vget<V>(ph, p), vld<V>(sj, 3 * T, (3 * p + 2) * T), A, B, C, D, fo);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) vstore(P.fout + ((size_t)p * 9 + i) * pl + node, 9 * (size_t)pl, fo[i]);
                 } else {
-                    // f*_j = w_j phi + h_j; stored: dev_j = f*_j - w_j phi(puller of j),
-                    // rounded to 16 bits.  The rest population (FP32) is what
-                    // makes the nine values the pullers reconstruct sum to phi.
-                    const float h1 = 0.5f * (A - D), h2 = 0.5f * (B - C);
-                    const float h5 = 0.25f * (C + D), h6 = 0.25f * (C - D);
-                    const float hdev[9] = {0.f, h1, h2, -h1, -h2, h5, h6, -h5, -h6};
-                    unsigned short *fo16 = (unsigned short *)P.fout + (size_t)p * 8 * pl + node;
-                    float r[9];
+                    // f*_j = w_j phi + h_j; stored: dev_j = f*_j - w_j phi(puller
+                    // of j), rounded to 16 bits (a phase pair's two deviations
+                    // in one word).  The rest population (FP32) is what makes
+                    // the nine values the pullers reconstruct sum to phi.
+                    const V phi = vget<V>(ph, p);
+                    const V h1 = vmul(vset<V>(0.5f), vsub(A, D)), h2 = vmul(vset<V>(0.5f), vsub(B, C));
+                    const V h5 = vmul(vset<V>(0.25f), vadd(C, D)), h6 = vmul(vset<V>(0.25f), vsub(C, D));
+                    const V zero = vset<V>(0.f);
+                    const V hdev[9] = {zero, h1, h2, vsub(zero, h1), vsub(zero, h2), h5, h6, vsub(zero, h5),
+                                       vsub(zero, h6)};
+                    V r[9];
 #pragma unroll
                     for (int j = 1; j < 9; ++j) {
                         const int sl = cy_of(j) > 0 ? sp : (cy_of(j) < 0 ? sm : s0);
-                        const float base = bounce(j) ? phi : s_phi[(sl * NS + p) * T + t + cx_of(j)];
-                        const unsigned short q = Store16<ST>::enc(__fmaf_rn(w_of(j), phi - base, hdev[j]));
-                        r[j] = __fmaf_rn(w_of(j), base, Store16<ST>::dec(q));
-                        fo16[(size_t)(j - 1) * pl] = q;
+                        const V base = bounce(j) ? phi : vld<V>(s_phi + (sl * NS + p) * T + t + cx_of(j), T, 0);
+                        const V dev = vfma(vset<V>(w_of(j)), vsub(phi, base), hdev[j]);
+                        if constexpr (sizeof(V) == 8) {
+                            const unsigned wd = Pack16<ST>::enc2(dev);
+                            ((unsigned *)P.fout)[dev_word(p / 2, j - 1, pl, node)] = wd;
+                            r[j] = vfma(vset<V>(w_of(j)), base, Pack16<ST>::dec2(wd));
+                        } else {
+                            const unsigned short q = Store16<ST>::enc(dev);
+                            ((unsigned short *)P.fout)[dev_tail(NS, j - 1, pl, node)] = q;
+                            r[j] = __fmaf_rn(w_of(j), base, Store16<ST>::dec(q));
+                        }
                     }
-                    float e13, e24, e57, e68, ea, eb, es, e0;
-                    const float s13 = two_sum(r[1], r[3], e13), s24 = two_sum(r[2], r[4], e24);
-                    const float s57 = two_sum(r[5], r[7], e57), s68 = two_sum(r[6], r[8], e68);
-                    const float sa = two_sum(s13, s24, ea), sb = two_sum(s57, s68, eb);
-                    const float S = two_sum(sa, sb, es);
-                    const float E = ((e13 + e24) + (e57 + e68)) + ((ea + eb) + es);
-                    const float a0 = two_sum(phi, -S, e0);
-                    P.f0out[(size_t)p * pl + node] = a0 + ((e0 + plo) - E);
+                    V e13, e24, e57, e68, ea, eb, es, e0;
+                    const V s13 = two_sum_v(r[1], r[3], e13), s24 = two_sum_v(r[2], r[4], e24);
+                    const V s57 = two_sum_v(r[5], r[7], e57), s68 = two_sum_v(r[6], r[8], e68);
+                    const V sa = two_sum_v(s13, s24, ea), sb = two_sum_v(s57, s68, eb);
+                    const V S = two_sum_v(sa, sb, es);
+                    const V E = vadd(vadd(vadd(e13, e24), vadd(e57, e68)), vadd(vadd(ea, eb), es));
+                    const V a0 = two_sum_v(phi, vsub(zero, S), e0);
+                    const V plo = vld<V>(sj, 3 * T, (3 * p + 2) * T);
+                    vstore(P.f0out + (size_t)p * pl + node, (size_t)pl, vadd(a0, vsub(vadd(e0, plo), E)));
                 }
-                P.phi[(size_t)p * pl + node] = phi;
-            }
+                vstore(P.phi + (size_t)p * pl + node, (size_t)pl, vget<V>(ph, p));
+            };
+#pragma unroll
+            for (int p = 0; p + 1 < NS; p += 2) collide(float2(), k2, p);
+            if (NS & 1) collide(0.f, k1, NS - 1);
 
             // flow collision, Eqs. (21)-(24), tau_g from Eq. (26)
             {
+                // (x, y) pairs: diagonal second moments (xx, yy), first
+                // moments, and (m7, m6) = (rho u_x, rho u_y)/3 + (F_x, F_y)/6
                 const float s2r = 2.f * rho / (6.f * mu + rho);   // 1/tau_g, tau_g = 3 mu/rho + 1/2
                 const float c2 = 1.f - s2r, h2 = 1.f - 0.5f * s2r;
-                const float Qxx = mx * ux, Qyy = my * uy, Qxy = 0.5f * (mx * uy + my * ux);
-                const float dQxx = mphx * ux - mpx * upx;
-                const float dQyy = mphy * uy - mpy * upy;
+                const float2 u2 = make_float2(ux, uy), F2 = make_float2(Fx, Fy), gr2 = make_float2(grx, gry);
+                const float2 Qd = vmul(make_float2(mx, my), u2);   // (Qxx, Qyy)
+                const float Qxy = 0.5f * (mx * uy + my * ux);
+                const float2 dQd = vsub(vmul(make_float2(mphx, mphy), u2), vmul(make_float2(mpx, mpy), make_float2(upx, upy)));
                 const float dQxy = 0.5f * ((mphx * uy + mphy * ux) - (mpx * upy + mpy * upx));
-                const float Mxx = 2.f * ux * Fx + dQxx + (2.f / 3.f) * ux * grx + (1.f / 3.f) * ugr;
-                const float Myy = 2.f * uy * Fy + dQyy + (2.f / 3.f) * uy * gry + (1.f / 3.f) * ugr;
+                const float2 Md = vadd(vfma(vset<float2>(2.f / 3.f), vmul(u2, gr2), vfma(vset<float2>(2.f), vmul(u2, F2), dQd)),
+                                       vset<float2>((1.f / 3.f) * ugr));   // (Mxx, Myy)
                 const float Mxy = ux * Fy + Fx * uy + dQxy + (1.f / 3.f) * (ux * gry + grx * uy);
-                const float m1 = jgx + Fx, m2 = jgy + Fy;
-                const float m3 = c2 * Pxx + s2r * (Pr + Qxx) + h2 * Mxx;
-                const float m4 = c2 * Pyy + s2r * (Pr + Qyy) + h2 * Myy;
+                const float2 m12 = vadd(make_float2(jgx, jgy), F2);
+                const float2 m34 = vfma(vset<float2>(c2), make_float2(Pxx, Pyy),
+                                        vfma(vset<float2>(s2r), vadd(vset<float2>(Pr), Qd), vmul(vset<float2>(h2), Md)));
                 const float m5 = c2 * Pxy + s2r * Qxy + h2 * Mxy;
-                const float m6 = rho * uy * (1.f / 3.f) + Fy * (1.f / 6.f);
-                const float m7 = rho * ux * (1.f / 3.f) + Fx * (1.f / 6.f);
-                const float m8 = (Pr + Qxx + Qyy) * (1.f / 3.f) + (Mxx + Myy) * (1.f / 6.f) - ugr * (1.f / 18.f);
-                const float gs[9] = {0.f,
-                                     0.5f * ((m1 - m7) + (m3 - m8)),
-                                     0.5f * ((m2 - m6) + (m4 - m8)),
-                                     0.5f * ((m7 - m1) + (m3 - m8)),
-                                     0.5f * ((m6 - m2) + (m4 - m8)),
+                const float2 m76 = vfma(vset<float2>(rho * (1.f / 3.f)), u2, vmul(F2, vset<float2>(1.f / 6.f)));
+                const float m6 = m76.y, m7 = m76.x;
+                const float m8 = (Pr + Qd.x + Qd.y) * (1.f / 3.f) + (Md.x + Md.y) * (1.f / 6.f) - ugr * (1.f / 18.f);
+                const float2 h34 = vsub(m34, vset<float2>(m8));
+                const float2 gs12 = vmul(vset<float2>(0.5f), vadd(vsub(m12, m76), h34));
+                const float2 gs34 = vmul(vset<float2>(0.5f), vadd(vsub(m76, m12), h34));
+                const float gs[9] = {0.f, gs12.x, gs12.y, gs34.x, gs34.y,
                                      0.25f * ((m5 + m6) + (m7 + m8)),
                                      0.25f * ((m6 - m5) + (m8 - m7)),
                                      0.25f * ((m5 - m6) + (m8 - m7)),

@@ -44,6 +44,41 @@ def test_noalloc_mass_matches_workspace_mass_twice_in_a_row():
     sim.close()
 
 
+@pytest.mark.parametrize("N", [2, 8])
+def test_noalloc_mass_smallest_and_largest_phase_count(N):
+    """N = 2 and N = 8 (the whole 512 x 9 scratch array in use): the volumes
+    of synthetic phase fields against an FP64 sum on the host, two calls in
+    a row with different fields; a planted out-of-range value raises the
+    flag."""
+    import torch
+    from paper_2306_06983_gb300.build import build
+    from paper_2306_06983_gb300 import nlbm
+
+    build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(40 + N)
+    n_nodes = 300 * 217   # ragged: not a multiple of the reduction's block size
+    mass = torch.full((N,), -1.0, dtype=torch.float64, device="cuda")
+    flag = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        phi = rng.dirichlet(np.ones(N), size=n_nodes).T[:N - 1].astype(np.float32)
+        dphi = torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+        st = nlbm.nlbm_phase_mass_noalloc(dphi.data_ptr(), N, n_nodes, mass.data_ptr(), flag.data_ptr(), stream)
+        assert st == nlbm.NLBM_OK
+        torch.cuda.synchronize()
+        p64 = phi.astype(np.float64)
+        ref = np.concatenate([p64.sum(axis=1), [(1.0 - p64.sum(axis=0)).sum()]])
+        np.testing.assert_allclose(mass.cpu().numpy(), ref, rtol=1e-12, atol=1e-9)
+        assert int(flag.item()) == 0, call
+    phi[0, 1234] = 7.0
+    dphi = torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    st = nlbm.nlbm_phase_mass_noalloc(dphi.data_ptr(), N, n_nodes, mass.data_ptr(), flag.data_ptr(), stream)
+    assert st == nlbm.NLBM_OK
+    torch.cuda.synchronize()
+    assert int(flag.item()) == 1
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2306_06983_gb300.build import build
@@ -57,3 +92,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = nlbm.nlbm_phase_mass_noalloc(buf.data_ptr(), 3, (1 << 28) + 1, buf.data_ptr(),
                                       flag.data_ptr(), 0)
     assert st == nlbm.NLBM_EINVAL
+    # below the range, and missing pointers: rejected before any GPU work
+    assert nlbm.nlbm_phase_mass_noalloc(buf.data_ptr(), 1, 4, buf.data_ptr(), flag.data_ptr(), 0) == nlbm.NLBM_EINVAL
+    assert nlbm.nlbm_phase_mass_noalloc(buf.data_ptr(), 3, 0, buf.data_ptr(), flag.data_ptr(), 0) == nlbm.NLBM_EINVAL
+    assert nlbm.nlbm_phase_mass_noalloc(0, 3, 4, buf.data_ptr(), flag.data_ptr(), 0) == nlbm.NLBM_EINVAL
+    assert nlbm.nlbm_phase_mass_noalloc(buf.data_ptr(), 3, 4, 0, flag.data_ptr(), 0) == nlbm.NLBM_EINVAL
+    assert nlbm.nlbm_phase_mass_noalloc(buf.data_ptr(), 3, 4, buf.data_ptr(), 0, 0) == nlbm.NLBM_EINVAL
