@@ -204,13 +204,12 @@ __global__ void tape_force_kernel(const StepParams P, AdjTape T)
 // tape fields and them.  Seeds at x: A.lf_out (f*), A.lg_out (g*), A.lphi_out
 // (phi(t): the next step's phi_prev and the loss), A.lu_out, A.lm_out.
 template <int NS>
-__global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
+__device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjTape &T, const AdjFields &A, unsigned k)
 {
-    pdl_wait();   // the previous kernel of the sweep has completed
     constexpr int N = NS + 1;
     constexpr int NP = N * (N - 1) / 2;
     const unsigned pl = P.plane;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+    {
         // ---------------- forward values at x
         float ph[N], lap[N], gx[NS], gy[NS], jx[NS], jy[NS], Rx[NS], Ry[NS], php[NS];
         float sph = 0.f, sl = 0.f, rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f, rho_prev = P.rhoN;
@@ -501,16 +500,16 @@ __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
     }
 }
 
+
 // rev2: F_c's stencil transposed (gather of the F adjoint at the
 // neighbours), then w, m_phi and the Model B source at the node.
 template <int NS>
-__global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
+__device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTape &T, const AdjFields &A, unsigned k)
 {
-    pdl_wait();   // the previous kernel of the sweep has completed
     constexpr int N = NS + 1;
     constexpr int NP = N * (N - 1) / 2;
     const unsigned pl = P.plane;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+    {
         const int x = k % P.nx, y = k / P.nx;
         // F_c(x) = (1/2 d_y w, -1/2 d_x w): w(z) enters F_c(z - c_i) with
         // weight 3 w_i c_i.
@@ -588,15 +587,15 @@ __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
     }
 }
 
+
 // rev3: the gradient and Laplacian stencils transposed: phi_p(z) entered
 // grad phi_p(z - c_i) with weight 3 w_i c_i and lap phi_p(z - c_i) with 6 w_i
 // (and lap phi_p(z) with -6 (1 - w_0)).
 template <int NS>
-__global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
+__device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjFields &A, unsigned k)
 {
-    pdl_wait();   // the previous kernel of the sweep has completed
     const unsigned pl = P.plane;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+    {
         const int x = k % P.nx, y = k / P.nx;
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -613,15 +612,15 @@ __global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
     }
 }
 
+
 // rev4: the pull and the moments transposed.  f_i(z) = f*_i(z - c_i) fed
 // phi(z) and j(z): the adjoint of f*_i at y is lphi(y + c_i) + c_i . lj(y + c_i);
 // likewise for the flow populations.  The results seed the previous step.
 template <int NS>
-__global__ void rev_pull_kernel(const StepParams P, AdjFields A)
+__device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFields &A, unsigned k)
 {
-    pdl_wait();   // the previous kernel of the sweep has completed
     const unsigned pl = P.plane;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < pl; k += gridDim.x * blockDim.x) {
+    {
         const int x = k % P.nx, y = k / P.nx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -634,6 +633,41 @@ __global__ void rev_pull_kernel(const StepParams P, AdjFields A)
             if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = A.lg_pull[(size_t)(i - 1) * pl + n];
         }
     }
+}
+
+
+// The four reverse passes, one launch each (every pass reads what the one
+// before wrote at the neighbours).
+template <int NS>
+__global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
+{
+    pdl_wait();   // the previous kernel of the sweep has completed
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
+        rev_collide_node<NS>(P, T, A, k);
+}
+
+template <int NS>
+__global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
+{
+    pdl_wait();
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
+        rev_source_node<NS>(P, T, A, k);
+}
+
+template <int NS>
+__global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
+{
+    pdl_wait();
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
+        rev_stencil_node<NS>(P, A, k);
+}
+
+template <int NS>
+__global__ void rev_pull_kernel(const StepParams P, AdjFields A)
+{
+    pdl_wait();
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
+        rev_pull_node<NS>(P, A, k);
 }
 
 constexpr int kRedThreads = 256;
@@ -674,21 +708,31 @@ int blocks_for(unsigned n)
     return (int)(b ? b : 1);
 }
 
+// Threads per block of the four reverse passes (one node per thread).
+// Measured on the 256^2 sweep (14.7-15.2 ms): 128-thread blocks 15.6 ms,
+// 64-thread 16.3 ms, 128 threads with the collision pass held to 85
+// registers 15.5 ms (at 1024^2 that one is 8.5 % faster, 11.6 against
+// 12.7 ms for 40 steps).
+constexpr int kRevThreads = 256;
+
 template <int NS>
 cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped, cudaStream_t st)
 {
     const int nb = blocks_for(P.plane);
+    const int nr = (int)((P.plane + kRevThreads - 1) / kRevThreads);
     if (!taped) {
         tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
         tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
         tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
     }
     // the four passes overlap each launch with the drain of the one before
+    // (measured: one cooperative launch with grid barriers between the
+    // passes is slower, 17.2 against 14.8 ms for the 256^2 sweep)
     cudaError_t e;
-    if ((e = launch_pdl(rev_collide_kernel<NS>, nb, 256, 0, st, P, T, A)) != cudaSuccess) return e;
-    if ((e = launch_pdl(rev_source_kernel<NS>, nb, 256, 0, st, P, T, A)) != cudaSuccess) return e;
-    if ((e = launch_pdl(rev_stencil_kernel<NS>, nb, 256, 0, st, P, A)) != cudaSuccess) return e;
-    return launch_pdl(rev_pull_kernel<NS>, nb, 256, 0, st, P, A);
+    if ((e = launch_pdl(rev_collide_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_source_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_stencil_kernel<NS>, nr, kRevThreads, 0, st, P, A)) != cudaSuccess) return e;
+    return launch_pdl(rev_pull_kernel<NS>, nr, kRevThreads, 0, st, P, A);
 }
 
 // dL/dphi_p for the solved phases from dL/dphi over all N phases (phi_N = 1 - sum).

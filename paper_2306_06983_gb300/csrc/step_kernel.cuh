@@ -1504,14 +1504,42 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     }
 }
 
+// Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
+// the staging rows (9 slots per phase, 10 with 16-bit storage; VEC: the
+// warps' pull windows and two rows of flow windows).
+template <int NS, int T, int ST, bool VEC = false>
+constexpr size_t step_smem_bytes()
+{
+    if (VEC && ST == 0) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
+    if (VEC)   // 16-bit deviation windows (2 bytes a value) and FP32 windows
+        return sizeof(float) * (size_t)T * (14 * NS + 3) +
+               (size_t)(T / 32) * (2 * kWin16 * (8 * NS + 16) + sizeof(float) * kWin * (2 * NS + 6));
+    return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
+}
+
+// Blocks per SM the step kernel is compiled for.  FP32 storage: three of 128
+// threads (up to 170 registers a thread; measured: the throughput is flat
+// between 12 and 16 resident warps and falls when the registers are squeezed
+// to fit more); from N = 7 on the row windows leave shared memory for two
+// blocks of 128 (or four of 64), so the registers may grow to 255 (2048^2
+// N = 7: 6,602 -> 8,562 MLUPS with 64-thread blocks).  16-bit storage: four
+// of 128 (128 registers), or as many as the shared memory of a block leaves
+// room for (from N = 6 on).
+template <int NS, int T, int ST, bool VEC>
+constexpr int step_min_blocks()
+{
+    if (ST == 0) return (NS >= 6 && VEC ? 256 : 384) / T;   // measured best at N = 7, 8 (255 registers)
+    constexpr size_t smem = step_smem_bytes<NS, T, ST, VEC>();
+    constexpr int by_smem = (int)((228u * 1024u) / (smem + 1024u));
+    constexpr int want = 512 / T;
+    return by_smem < 1 ? 1 : (by_smem < want ? by_smem : want);
+}
+
 // Grid: one block per (strip, row chunk), strips of T - 4 columns, strip
 // index fastest.  TY > 0: chunks of TY rows; TY = 0: chunk k of `chunks`
 // covers rows [k ny / chunks, (k + 1) ny / chunks).
 template <int NS, int MODEL, int T, int ST, bool VEC, bool TAPE = false>
-// FP32: three blocks of 128 threads per SM, up to 170 registers a thread
-// (measured: the throughput is flat between 12 and 16 resident warps and
-// falls when the registers are squeezed to fit more).  16-bit storage: four.
-__global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
+__global__ void __launch_bounds__(T, (step_min_blocks<NS, T, ST, VEC>()))
     step_kernel(const StepParams P, const int TY, const int chunks, const int strips)
 {
     extern __shared__ __align__(16) float smem[];
@@ -1527,19 +1555,6 @@ __global__ void __launch_bounds__(T, (ST == 0 ? 384 : 512) / T)
     }
     if (ty <= 0 || y0 >= P.ny) return;
     step_tile<NS, MODEL, T, ST, VEC, TAPE>(P, s * (T - 4), y0, ty, smem);
-}
-
-// Dynamic shared memory of step_tile: phi ring, w ring, own-node j ring and
-// the staging rows (9 slots per phase, 10 with 16-bit storage; VEC: the
-// warps' pull windows and two rows of flow windows).
-template <int NS, int T, int ST, bool VEC = false>
-constexpr size_t step_smem_bytes()
-{
-    if (VEC && ST == 0) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
-    if (VEC)   // 16-bit deviation windows (2 bytes a value) and FP32 windows
-        return sizeof(float) * (size_t)T * (14 * NS + 3) +
-               (size_t)(T / 32) * (2 * kWin16 * (8 * NS + 16) + sizeof(float) * kWin * (2 * NS + 6));
-    return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
 }
 
 // Resident blocks of one kernel variant on device dev (the dynamic

@@ -706,11 +706,19 @@ def _make_function():
             return out
 
         @staticmethod
+        @torch.autograd.function.once_differentiable
         def backward(ctx, grad_out):
+            # the run (checkpoints, tapes) is released after one reverse
+            # sweep: a second backward through the same graph is refused
+            if ctx.run is None:
+                raise RuntimeError(
+                    "nphase_lbm: the adjoint run was released by the first backward; "
+                    "retain_graph=True is not supported -- run the forward again")
             g0, gs, gm = ctx.run.backward(grad_out.contiguous())
             N = ctx.N
             gpairs = torch.tensor([gs[p, q] for p, q in pair_list(N)], dtype=ctx.sdtype)
             ctx.run.close()
+            ctx.run = None
             return g0, gpairs, torch.tensor(gm, dtype=ctx.sdtype), None, None, None
 
     return NPhaseLBM

@@ -216,6 +216,23 @@ def test_autograd_function_and_descent():
     assert float(L2) < float(L.detach())
 
 
+def test_second_backward_is_refused():
+    """The Function releases its run after one reverse sweep: a second
+    backward through the same graph (retain_graph=True) raises a clear
+    error instead of returning gradients of a released run."""
+    import torch
+    from paper_2306_06983_gb300.nlbm import nphase_lbm
+    p, phi0 = W.adjoint_problem(32, 32)
+    sig = torch.tensor(S0, dtype=torch.float64, requires_grad=True)
+    mob = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    out = nphase_lbm(torch.from_numpy(phi0.astype(np.float32)).cuda(), sig, mob, p, 10, 5)
+    L = (out.double() ** 2).sum()
+    L.backward(retain_graph=True)
+    assert sig.grad is not None
+    with pytest.raises(RuntimeError, match="retain_graph"):
+        L.backward()
+
+
 def test_taped_sweep_matches_tape_passes():
     """The reverse sweep takes each step's intermediate fields from the taping
     forward kernel that rebuilds the segment; the single-step entry point
