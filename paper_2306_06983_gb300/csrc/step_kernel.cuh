@@ -724,17 +724,38 @@ __device__ __forceinline__ void grad_lap9(V sw, V s, V se, V w, V ce, V e, V nw,
     }
 }
 
-// Phases p (and p + 1) of the 3x3 window of the phi ring at column c.
+// Shared-memory rings of per-phase values (phi, j): a row of a ring holds
+// [NS / 2 rounded up][W][2] floats, phases 2q and 2q + 1 side by side, so a
+// phase pair is one 8-byte access.  ring_even(NS) floats per column of a row.
+__host__ __device__ constexpr int ring_even(int NS) { return NS + (NS & 1); }
+__device__ __forceinline__ int ring_idx(int W, int p, int c) { return ((p >> 1) * W + c) * 2 + (p & 1); }
+template <class V> __device__ __forceinline__ V rld(const float *row, int W, int p, int c);
+template <> __device__ __forceinline__ float rld<float>(const float *row, int W, int p, int c)
+{
+    return row[ring_idx(W, p, c)];
+}
+template <> __device__ __forceinline__ float2 rld<float2>(const float *row, int W, int p, int c)
+{
+    return *reinterpret_cast<const float2 *>(row + ring_idx(W, p, c));
+}
+__device__ __forceinline__ void rst(float *row, int W, int p, int c, float v) { row[ring_idx(W, p, c)] = v; }
+__device__ __forceinline__ void rst(float *row, int W, int p, int c, float2 v)
+{
+    *reinterpret_cast<float2 *>(row + ring_idx(W, p, c)) = v;
+}
+
+// Phases p (and p + 1) of the 3x3 window of the phi ring at column c (rows
+// sm, s0, sp of the ring).
 template <class V, bool LAP>
 __device__ __forceinline__ void window_v(const float *s_phi, int W, int NS, int sm, int s0, int sp, int c, int p,
                                          V &ce, V &gx, V &gy, V &lap)
 {
-    const float *rm = s_phi + (sm * NS + p) * W + c;
-    const float *r0 = s_phi + (s0 * NS + p) * W + c;
-    const float *rp = s_phi + (sp * NS + p) * W + c;
-    ce = vld<V>(r0, W, 0);
-    grad_lap9<V, LAP>(vld<V>(rm, W, -1), vld<V>(rm, W, 0), vld<V>(rm, W, 1), vld<V>(r0, W, -1), ce,
-                      vld<V>(r0, W, 1), vld<V>(rp, W, -1), vld<V>(rp, W, 0), vld<V>(rp, W, 1), gx, gy, lap);
+    const int R = ring_even(NS) * W;   // floats per ring row
+    const float *rm = s_phi + sm * R, *r0 = s_phi + s0 * R, *rp = s_phi + sp * R;
+    ce = rld<V>(r0, W, p, c);
+    grad_lap9<V, LAP>(rld<V>(rm, W, p, c - 1), rld<V>(rm, W, p, c), rld<V>(rm, W, p, c + 1), rld<V>(r0, W, p, c - 1),
+                      ce, rld<V>(r0, W, p, c + 1), rld<V>(rp, W, p, c - 1), rld<V>(rp, W, p, c),
+                      rld<V>(rp, W, p, c + 1), gx, gy, lap);
 }
 
 // phi, grad phi (Eq. (27)) and, with LAP, lap phi of all N phases from one
@@ -946,10 +967,11 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
     // stage B and the inner T - 4 (the strip) complete their node in stage
     // C, so no warp runs a stage twice for halo nodes.
     constexpr int W = T - 4;                 // strip width
-    float *s_phi = smem;                     // [5][NS][T]   phi(t) rows r-2..r+2
-    float *s_w = s_phi + 5 * NS * T;         // [3][T]       w = m_phi,x u_y - u_x m_phi,y, rows r-1..r+1
-    float *s_j = s_w + 3 * T;                // [3][3NS][T]  j_x, j_y, phi_lo of own nodes
-    float *s_F = s_j + 9 * NS * T;           // [9NS][T]     staged pulled f of the next row
+    constexpr int NE = ring_even(NS);       // phases per ring row, rounded up to pairs
+    float *s_phi = smem;                     // [5][NE/2][T][2] phi(t) rows r-2..r+2 (see ring_idx)
+    float *s_w = s_phi + 5 * NE * T;         // [3][T]       w = m_phi,x u_y - u_x m_phi,y, rows r-1..r+1
+    float *s_j = s_w + 3 * T;                // [3][3][NE/2][T][2] j_x, j_y, phi_lo of own nodes
+    float *s_F = s_j + 9 * NE * T;           // [9NS][T]     staged pulled f of the next row
                                              // ([10NS][T] with 16-bit storage, see prefetch_pull16;
                                              // VEC: [T/32][9NS][kWin] row windows)
     float *s_G = s_F + (T / 32) * 9 * NS * kWin;   // VEC: [2][T/32][8][kWin] g windows of two rows
@@ -1111,16 +1133,22 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 #pragma unroll
                 for (int p = 0; p < NS; ++p) ph[p] += k2 * sp[p];
             }
-            const int s5 = a5;
+            float *prow = s_phi + a5 * NE * T;
 #pragma unroll
-            for (int p = 0; p < NS; ++p) s_phi[(s5 * NS + p) * T + t] = ph[p];
+            for (int p = 0; p + 1 < NS; p += 2) rst(prow, T, p, t, vget<float2>(ph, p));
+            if (NS & 1) rst(prow, T, NS - 1, t, ph[NS - 1]);
             if (own && ra >= y0 && ra < y0 + TYe) {
-                const int s3 = a3;
+                float *jrow = s_j + a3 * 3 * NE * T;   // j_x, then j_y, then phi_lo rows
 #pragma unroll
-                for (int p = 0; p < NS; ++p) {
-                    s_j[(s3 * 3 * NS + 3 * p) * T + t] = jx[p];
-                    s_j[(s3 * 3 * NS + 3 * p + 1) * T + t] = jy[p];
-                    s_j[(s3 * 3 * NS + 3 * p + 2) * T + t] = plo[p];
+                for (int p = 0; p + 1 < NS; p += 2) {
+                    rst(jrow, T, p, t, vget<float2>(jx, p));
+                    rst(jrow + NE * T, T, p, t, vget<float2>(jy, p));
+                    rst(jrow + 2 * NE * T, T, p, t, vget<float2>(plo, p));
+                }
+                if (NS & 1) {
+                    rst(jrow, T, NS - 1, t, jx[NS - 1]);
+                    rst(jrow + NE * T, T, NS - 1, t, jy[NS - 1]);
+                    rst(jrow + 2 * NE * T, T, NS - 1, t, plo[NS - 1]);
                 }
             }
             if (!VEC && it + 1 < TYe + 4) {
@@ -1360,15 +1388,15 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
             (void)bounce;
             const CollCoef<float2> k2(P.s1, ux, uy, upx, upy);
             const CollCoef<float> k1(P.s1, ux, uy, upx, upy);
-            const float *sj = s_j + (s3 * 3 * NS) * T + t;   // j_x, j_y, phi_lo of phase p at sj + 3 p T
+            const float *sjx = s_j + s3 * 3 * NE * T, *sjy = sjx + NE * T, *slo = sjy + NE * T;
             auto collide = [&](auto tag, const auto &k, int p) {
                 using V = decltype(tag);
                 V A, B, C, D;
-                phase_moments<V>(vget<V>(ph, p), vld<V>(sj, 3 * T, 3 * p * T), vld<V>(sj, 3 * T, (3 * p + 1) * T),
-                                 vget<V>(php, p), vget<V>(Rcx, p), vget<V>(Rcy, p), k, A, B, C, D);
+                phase_moments<V>(vget<V>(ph, p), rld<V>(sjx, T, p, t), rld<V>(sjy, T, p, t), vget<V>(php, p),
+                                 vget<V>(Rcx, p), vget<V>(Rcy, p), k, A, B, C, D);
                 if constexpr (ST == 0) {
                     V fo[9];
-                    phase_populations<V>(vget<V>(ph, p), vld<V>(sj, 3 * T, (3 * p + 2) * T), A, B, C, D, fo);
+                    phase_populations<V>(vget<V>(ph, p), rld<V>(slo, T, p, t), A, B, C, D, fo);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) vstore(P.fout + ((size_t)p * 9 + i) * pl + node, 9 * (size_t)pl, fo[i]);
                 } else {
@@ -1386,7 +1414,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 #pragma unroll
                     for (int j = 1; j < 9; ++j) {
                         const int sl = cy_of(j) > 0 ? sp : (cy_of(j) < 0 ? sm : s0);
-                        const V base = bounce(j) ? phi : vld<V>(s_phi + (sl * NS + p) * T + t + cx_of(j), T, 0);
+                        const V base = bounce(j) ? phi : rld<V>(s_phi + sl * NE * T, T, p, t + cx_of(j));
                         const V dev = vfma(vset<V>(w_of(j)), vsub(phi, base), hdev[j]);
                         if constexpr (sizeof(V) == 8) {
                             const unsigned wd = Pack16<ST>::enc2(dev);
@@ -1405,7 +1433,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
                     const V S = two_sum_v(sa, sb, es);
                     const V E = vadd(vadd(vadd(e13, e24), vadd(e57, e68)), vadd(vadd(ea, eb), es));
                     const V a0 = two_sum_v(phi, vsub(zero, S), e0);
-                    const V plo = vld<V>(sj, 3 * T, (3 * p + 2) * T);
+                    const V plo = rld<V>(slo, T, p, t);
                     vstore(P.f0out + (size_t)p * pl + node, (size_t)pl, vadd(a0, vsub(vadd(e0, plo), E)));
                 }
                 vstore(P.phi + (size_t)p * pl + node, (size_t)pl, vget<V>(ph, p));
@@ -1466,8 +1494,8 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 #pragma unroll
                 for (int p = 0; p < NS; ++p) {
                     tp[(size_t)p * pl] = ph[p];
-                    tp[(size_t)(NS + 2 * p) * pl] = s_j[(s3 * 3 * NS + 3 * p) * T + t];
-                    tp[(size_t)(NS + 2 * p + 1) * pl] = s_j[(s3 * 3 * NS + 3 * p + 1) * T + t];
+                    tp[(size_t)(NS + 2 * p) * pl] = rld<float>(sjx, T, p, t);
+                    tp[(size_t)(NS + 2 * p + 1) * pl] = rld<float>(sjy, T, p, t);
                     tp[(size_t)(3 * NS + 8 + 2 * p) * pl] = gx[p];
                     tp[(size_t)(3 * NS + 9 + 2 * p) * pl] = gy[p];
                     tp[(size_t)(5 * NS + 8 + p) * pl] = lap[p];
@@ -1510,11 +1538,12 @@ __device__ __forceinline__ void step_tile(const StepParams &P, const int x0, con
 template <int NS, int T, int ST, bool VEC = false>
 constexpr size_t step_smem_bytes()
 {
-    if (VEC && ST == 0) return sizeof(float) * ((size_t)T * (14 * NS + 3) + (size_t)(T / 32) * kWin * (9 * NS + 16));
+    constexpr size_t rings = (size_t)T * (14 * ring_even(NS) + 3);   // phi, w and j rings (floats)
+    if (VEC && ST == 0) return sizeof(float) * (rings + (size_t)(T / 32) * kWin * (9 * NS + 16));
     if (VEC)   // 16-bit deviation windows (2 bytes a value) and FP32 windows
-        return sizeof(float) * (size_t)T * (14 * NS + 3) +
+        return sizeof(float) * rings +
                (size_t)(T / 32) * (2 * kWin16 * (8 * NS + 16) + sizeof(float) * kWin * (2 * NS + 6));
-    return sizeof(float) * (size_t)T * ((ST == 0 ? 23 : 24) * NS + 3);
+    return sizeof(float) * (rings + (size_t)T * (ST == 0 ? 9 : 10) * NS);
 }
 
 // Blocks per SM the step kernel is compiled for.  FP32 storage: three of 128
