@@ -136,6 +136,20 @@ nlbm_status nlbm_create(const nlbm_params *p, void *dev_workspace, size_t worksp
  * Eq. (22) with P = 0.  Resets the step counter.  Asynchronous. */
 nlbm_status nlbm_set_phi(nlbm_sim *s, const float *dev_phi);
 
+/* Start the simulation in motion: after nlbm_set_phi() and before the first
+ * step, give the fluid the velocity dev_u [2][ny][nx] (u_x plane, then u_y;
+ * device memory, read before the call's work completes on the stream).  The
+ * paper starts every case at rest and gives no initial state in motion; this
+ * one is the equilibrium of each set at u (Eqs. (19), (22)) with
+ * m = rho u + m_phi, m_phi of the initial fields (Eq. (13)), the pressure in
+ * lambda_i chosen so that Eq. (25c) recovers P = 0 from these populations,
+ * and the initial values as the previous values of the first step's time
+ * derivatives (u(-1) = u, phi(-1) = phi(0), m_phi(-1) = m_phi(0)), so that a
+ * flow in steady translation starts without a jump.  FP32 storage and no
+ * wetting walls (else ENOTSUP); EINVAL after a step has been taken.  Two
+ * kernel launches on the simulation's stream. */
+nlbm_status nlbm_set_velocity(nlbm_sim *s, const float *dev_u);
+
 /* As nlbm_set_phi() with host_phi [N-1][ny][nx] in host memory; the copy is
  * enqueued on the simulation's stream (synchronizes when host_phi is
  * pageable). */

@@ -344,6 +344,32 @@ nlbm_status nlbm_set_phi_host(nlbm_sim *s, const float *host_phi)
     return NLBM_OK;
 }
 
+nlbm_status nlbm_set_velocity(nlbm_sim *s, const float *dev_u)
+{
+    if (!s || !dev_u) return NLBM_EINVAL;
+    if (s->half()) {
+        set_err(s->err, "a state in motion is set for FP32 population storage only");
+        return NLBM_ENOTSUP;
+    }
+    if (s->kp.wet) {
+        set_err(s->err, "a state in motion is not set with wetting walls");
+        return NLBM_ENOTSUP;
+    }
+    if (s->steps != 0) {
+        set_err(s->err, "set the velocity after nlbm_set_phi and before the first step");
+        return NLBM_EINVAL;
+    }
+    const int c = s->cur;
+    // the populations of state c; u(c) becomes the first step's previous
+    // velocity, and the other velocity buffer holds P' until the first step
+    // overwrites it
+    const StepParams kp = step_params(s, c ^ 1, c);
+    cudaError_t e = launch_velocity_state(s->ns, s->model, kp, dev_u, s->u(c), s->u(c ^ 1), s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "velocity initial state");
+    s->launches += 2;
+    return NLBM_OK;
+}
+
 nlbm_status nlbm_step(nlbm_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return NLBM_EINVAL;

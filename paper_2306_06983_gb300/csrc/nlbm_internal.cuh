@@ -19,9 +19,11 @@
 //   mphi [2][plane]     m_phi of the last step
 //   P   [plane]         pressure, written on request
 // With 16-bit storage (bfloat16 or binary16) the moving populations are kept
-// as deviations (f [N-1][8][plane] and g [8][plane], 2 bytes each), the rest
-// populations f0 [N-1][plane] in FP32, and phi and P are double-buffered:
-// the puller adds w_i phi(puller, t) and 3 w_i P(source, t) back.
+// as deviations, 2 bytes each (f: phases 2q and 2q + 1 share a 32-bit word
+// per direction and node, [(N-1)/2][8][plane] words, an odd last phase in
+// [8][plane] 16-bit planes after them; g [8][plane]), the rest populations
+// f0 [N-1][plane] in FP32, and phi and P are double-buffered: the puller adds
+// w_i phi(puller, t) and 3 w_i P(source, t) back.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,7 +53,7 @@ struct StepParams {
     float s1;                  // 1 / tau_f, tau_f = 0.5 + 3 M (Eq. (20))
     float model_n;             // Model A exponent n
     int model_n_int;           // n when it is an integer in 1..8, else 0
-    const float *fin;          // FP32: [N-1][9][plane]; 16-bit: [N-1][8][plane] deviations
+    const float *fin;          // FP32: [N-1][9][plane]; 16-bit: deviations (see above)
     float *fout;
     const float *f0in;         // 16-bit storage only: FP32 rest populations [N-1][plane]
     float *f0out;
@@ -134,6 +136,12 @@ cudaError_t launch_batch_step(int ns, int tx, const StepParams *d_params, const 
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_init(int ns, const StepParams &p, cudaStream_t st);
+// A state in motion (velocity.cu): p describes the state set by launch_init
+// (p.phi, p.fout, p.gout, p.mphi); u0 [2][plane] the velocity, u_prev the
+// velocity buffer the first step reads as its previous one, p_scratch one
+// plane the first step overwrites.  FP32 storage.
+cudaError_t launch_velocity_state(int ns, int model, const StepParams &p, const float *u0, float *u_prev,
+                                  float *p_scratch, cudaStream_t st);
 cudaError_t launch_export(int ns, const float *phi_aux, const float *u, const float *P,
                           unsigned plane, float *phi_out, float *u_out, float *p_out,
                           cudaStream_t st);

@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
         "nlbm_create": (st, [P(nlbm_params), vp, ctypes.c_size_t, vp, P(vp)]),
         "nlbm_set_phi": (st, [vp, vp]),
         "nlbm_set_phi_host": (st, [vp, vp]),
+        "nlbm_set_velocity": (st, [vp, vp]),
         "nlbm_step": (st, [vp, ctypes.c_int64]),
         "nlbm_get_moments": (st, [vp, vp, vp, vp]),
         "nlbm_get_moments_host": (st, [vp, vp, vp, vp]),
@@ -201,6 +202,10 @@ def nlbm_set_phi_host(h, host_ptr: int):
     _check(load_library().nlbm_set_phi_host(h, ctypes.c_void_p(host_ptr)), h)
 
 
+def nlbm_set_velocity(h, dev_ptr: int):
+    _check(load_library().nlbm_set_velocity(h, ctypes.c_void_p(dev_ptr)), h)
+
+
 def nlbm_step(h, nsteps: int):
     _check(load_library().nlbm_step(h, int(nsteps)), h)
 
@@ -327,6 +332,19 @@ class Simulation:
         assert t.device.type == "cpu" and t.dtype == self.torch.float32 and t.is_contiguous()
         assert t.shape == (self.N - 1, self.ny, self.nx)
         nlbm_set_phi_host(self.h, t.data_ptr())
+
+    def set_velocity(self, u0):
+        """Start in motion (after set_phi, before the first step): u0 [2, ny,
+        nx] (u_x, u_y) as a tensor or array, or a pair (u_x, u_y) for a
+        uniform flow."""
+        torch = self.torch
+        t = torch.as_tensor(np.asarray(u0) if not isinstance(u0, torch.Tensor) else u0, dtype=torch.float32)
+        if t.shape == (2,):
+            t = t[:, None, None].expand(2, self.ny, self.nx)
+        t = t.to(self.device).contiguous()
+        assert t.shape == (2, self.ny, self.nx), t.shape
+        self._u0 = t   # kept alive until the stream has read it
+        nlbm_set_velocity(self.h, t.data_ptr())
 
     def step(self, n: int):
         nlbm_step(self.h, n)
