@@ -248,6 +248,7 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
             sim.set_phi(phi0.astype(np.float32))
             m0 = sim.phase_mass()
             sim.step(args.warmup)
+            tile = sim.autotune(20)[:2]
             ms = timed(stream, sim.step, args.steps)
             phi, u = (t.cpu().numpy() for t in sim.moments()[:2])
             m1 = sim.phase_mass(allow_diverged=True)
@@ -263,7 +264,7 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
                 # the minimum for 16-bit populations with every population
                 # (the rest one too) in 16 bits and N + 3 FP32 fields
                 "roofline_frac_at_min_bytes": round((44 * N + 20) * lups / (ms / 1e3) / 1e9 / peak, 4),
-                "min_bytes_per_lup": 44 * N + 20,
+                "min_bytes_per_lup": 44 * N + 20, "tile": list(tile),
                 "of_f32_headline": None,
                 "vs_f32_after_same_steps": {
                     "steps": args.warmup + args.steps,
@@ -275,12 +276,12 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         # the other model on the same workload (Model A with n = 1 beside the
         # Model B headline, or B beside A), FP32
         other = "A" if args.model == "B" else "B"
-        q, _ = W.disks_2048(other)
-        q = dict(q, storage="f32")
+        q = dict(p, model=other, model_a_n=1.0, storage="f32")
         sim = Simulation(q, stream=stream)
         sim.set_phi(phi0.astype(np.float32))
         m0 = sim.phase_mass()
         sim.step(args.warmup)
+        tile = sim.autotune(20)[:2]
         ms = timed(stream, sim.step, args.steps)
         m1 = sim.phase_mass(allow_diverged=True)
         sim.close()
@@ -289,7 +290,7 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         bpl = bytes_per_lup(N)
         forms[f"model_{other}"] = {
             "workload": WORKLOAD + f", Model {other}" + (" (n = 1)" if other == "A" else ""),
-            "value": round(lups / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
+            "value": round(lups / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5), "tile": list(tile),
             "algorithmic_bytes_per_lup": bpl,
             "roofline_frac": round(bpl * lups / (ms / 1e3) / 1e9 / peak, 4),
             "mass_drift_rel": float((np.abs(m1 - m0) / np.abs(m0)).max()),
@@ -410,6 +411,7 @@ def measure_rti(args, timed, stream, peak):
     sim.set_phi(phi0.astype(np.float32))
     m0 = sim.phase_mass()
     sim.step(args.warmup)
+    tile = sim.autotune(20)[:2]
     l0 = sim.kernel_launches
     ms = timed(stream, sim.step, args.steps)
     launches = sim.kernel_launches - l0
@@ -422,12 +424,12 @@ def measure_rti(args, timed, stream, peak):
                     "sqrt(g d) = 0.04, walls top and bottom, Model B, FP32",
         "nodes": nodes, "value": round(nodes / ms / 1e3, 2), "unit": "MLUPS", "ms_per_step": round(ms, 5),
         "algorithmic_bytes_per_lup": bpl, "roofline_frac": round(bpl * nodes / (ms / 1e3) / 1e9 / peak, 4),
-        "gpu_launches": launches, "mass_drift_rel": drift,
+        "gpu_launches": launches, "mass_drift_rel": drift, "tile": list(tile),
     }
 
 
-def measure_adjoint(timed):
-    """Gradient study (256x256 periodic, N = 3, Model B, 500 steps, a
+def measure_adjoint(timed, n=256):
+    """Gradient study (n x n periodic, 256 by default, N = 3, Model B, 500 steps, a
     checkpoint every 50, smooth unit vectors delta = 1e-3): L = 1/2 |phi(T) -
     phi_hat|^2 with phi_hat from sigma = (0.012, 0.008, 0.010); gradients with
     respect to the three tensions, the mobility and the initial fields from
@@ -438,7 +440,7 @@ def measure_adjoint(timed):
     from paper_2306_06983_gb300 import workloads as W
     from paper_2306_06983_gb300.nlbm import AdjointRun, Simulation, pair_list
     T, every = 500, 50
-    p, phi0 = W.adjoint_problem(256, 256)
+    p, phi0 = W.adjoint_problem(n, n)
     phi0 = phi0.astype(np.float32)
     N = p["n_phases"]
 
@@ -484,9 +486,9 @@ def measure_adjoint(timed):
     graph = run.uses_graph
     run.close()
     fwd, bwd = float(np.median(fwds)), float(np.median(bwds))
-    nodes = 256 * 256
+    nodes = n * n
     return {
-        "workload": "256x256 periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
+        "workload": f"{n}x{n} periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
                     "v/sqrt(|v|^2+1e-6); L2 mismatch of phi(T) against the sigma=(0.012,0.008,0.010) run",
         "value": round(nodes * T / ((fwd + bwd) / 1e3) / 1e6, 2), "unit": "MLUPS (differentiated)",
         "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3), "backward_over_forward": round(bwd / fwd, 2),
@@ -520,6 +522,25 @@ def run_forms_only(args):
     print(json.dumps({"metric": METRIC, "forms": forms}), flush=True)
 
 
+def run_adjoint_only(args):
+    """Profiling aid: the adjoint form alone on an n x n lattice."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+    def timed(stream, fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+    print(json.dumps({"metric": METRIC, "forms": {"adjoint": measure_adjoint(timed, args.only_adjoint)}}),
+          flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -550,10 +571,14 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = Simulation(p, stream=stream)
-        if args.tile:
-            sim.set_tile(*args.tile)
         sim.set_phi(phi0.astype(np.float32))
         sim.step(args.warmup)
+        # tile shape: the library's autotuner (outside the timed region; the
+        # result of a step does not depend on it), unless --tile fixes it
+        if args.tile:
+            sim.set_tile(*args.tile)
+        else:
+            sim.autotune(20)
         stream.synchronize()
 
         # ---------------------------------------------- device-timed region
@@ -587,8 +612,7 @@ def run_gpu(args):
         out_u = torch.empty((2, ny, nx), dtype=torch.float32).pin_memory()
         out_p = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
         sim2 = Simulation(p, stream=stream)
-        if args.tile:
-            sim2.set_tile(*args.tile)
+        sim2.set_tile(*tile)
         stream.synchronize()
         if world > 1:
             dist.barrier()
@@ -691,11 +715,15 @@ def main():
                     help="skip the 16-bit storage and ensemble forms measured beside the headline")
     ap.add_argument("--only-forms", action="store_true",
                     help="profiling aid: time only the forms (on --lattice if given), print them")
+    ap.add_argument("--only-adjoint", type=int, default=0, metavar="N",
+                    help="profiling aid: time only the adjoint form on an N x N lattice, print it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_adjoint:
+        run_adjoint_only(args)
     elif args.only_forms:
         run_forms_only(args)
     else:

@@ -207,6 +207,20 @@ int64_t nlbm_kernel_launches(const nlbm_sim *s);
 nlbm_status nlbm_set_tile(nlbm_sim *s, int32_t tx, int32_t ty);
 nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty);
 
+/* Tile autotuner: for every tile shape tx in {64, 128, 256} (wider strips
+ * than the lattice needs are skipped) x ty in {0, 8, 12, 16, 20, 24, 32,
+ * 48}, one untimed step and then steps_per_trial (>= 1) steps timed with
+ * CUDA events on the simulation's stream, each trial from the state saved
+ * in dev_scratch (device memory, 16-byte aligned, at least
+ * nlbm_state_bytes()); keeps the fastest shape.  The result of a step does
+ * not depend on the tile (every node is computed by the same code from the
+ * same inputs), and the state and step counter are those of the call on
+ * return; the trial launches count in nlbm_kernel_launches().  Any output
+ * pointer may be NULL.  ENOMEM when the scratch is too small.
+ * Synchronizes. */
+nlbm_status nlbm_autotune(nlbm_sim *s, void *dev_scratch, size_t scratch_bytes, int32_t steps_per_trial,
+                          int32_t *best_tx, int32_t *best_ty, float *best_ms_per_step);
+
 /* Per-phase volume sum_x phi_p, p = 1..N, for callers that cannot allocate
  * device memory at all -- neither through this library's workspace nor their
  * own allocator: code that runs where cudaMalloc is forbidden or unsafe (a

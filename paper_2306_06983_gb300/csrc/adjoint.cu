@@ -215,15 +215,15 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
         float sph = 0.f, sl = 0.f, rho = P.rhoN, mu = P.muN, grx = 0.f, gry = 0.f, rho_prev = P.rhoN;
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
-            ph[p] = T.phi[(size_t)p * pl + k];
-            lap[p] = T.lap[(size_t)p * pl + k];
-            gx[p] = T.grad[(size_t)(2 * p) * pl + k];
-            gy[p] = T.grad[(size_t)(2 * p + 1) * pl + k];
-            jx[p] = T.j[(size_t)(2 * p) * pl + k];
-            jy[p] = T.j[(size_t)(2 * p + 1) * pl + k];
-            Rx[p] = T.R[(size_t)(2 * p) * pl + k];
-            Ry[p] = T.R[(size_t)(2 * p + 1) * pl + k];
-            php[p] = P.phi_prev[(size_t)p * pl + k];
+            ph[p] = __ldg(T.phi + (size_t)p * pl + k);
+            lap[p] = __ldg(T.lap + (size_t)p * pl + k);
+            gx[p] = __ldg(T.grad + (size_t)(2 * p) * pl + k);
+            gy[p] = __ldg(T.grad + (size_t)(2 * p + 1) * pl + k);
+            jx[p] = __ldg(T.j + (size_t)(2 * p) * pl + k);
+            jy[p] = __ldg(T.j + (size_t)(2 * p + 1) * pl + k);
+            Rx[p] = __ldg(T.R + (size_t)(2 * p) * pl + k);
+            Ry[p] = __ldg(T.R + (size_t)(2 * p + 1) * pl + k);
+            php[p] = __ldg(P.phi_prev + (size_t)p * pl + k);
             sph += ph[p];
             sl += lap[p];
             rho += P.drho[p] * ph[p];
@@ -234,13 +234,16 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
         }
         ph[NS] = 1.f - sph;
         lap[NS] = -sl;
+        double gacc[NP + 1];   // updated at the end; loaded before the first store
+#pragma unroll
+        for (int q = 0; q <= NP; ++q) gacc[q] = A.gacc[(size_t)q * pl + k];
         float g[9];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) g[i] = T.g[(size_t)(i - 1) * pl + k];
-        const float Fx = T.F[k], Fy = T.F[pl + k];
-        const float mphx = T.mphi[k], mphy = T.mphi[pl + k];
-        const float upx = P.uin[k], upy = P.uin[pl + k];
-        const float mpx = P.mphi[k], mpy = P.mphi[pl + k];   // m_phi of step t-1
+        for (int i = 1; i < 9; ++i) g[i] = __ldg(T.g + (size_t)(i - 1) * pl + k);
+        const float Fx = __ldg(T.F + k), Fy = __ldg(T.F + pl + k);
+        const float mphx = __ldg(T.mphi + k), mphy = __ldg(T.mphi + pl + k);
+        const float upx = __ldg(P.uin + k), upy = __ldg(P.uin + pl + k);
+        const float mpx = __ldg(P.mphi + k), mpy = __ldg(P.mphi + pl + k);   // m_phi of step t-1
         const float sg = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
         const float jgx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
         const float jgy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
@@ -267,18 +270,18 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
         for (int p = 0; p < N; ++p) { a_ph[p] = 0.f; a_lap[p] = 0.f; }
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
-            a_ph[p] = A.lphi_out[(size_t)p * pl + k];
+            a_ph[p] = __ldg(A.lphi_out + (size_t)p * pl + k);
             a_gx[p] = a_gy[p] = a_Rx[p] = a_Ry[p] = a_php[p] = 0.f;
         }
-        float a_ux = A.lu_out[k], a_uy = A.lu_out[pl + k];
-        float a_mphx = A.lm_out[k], a_mphy = A.lm_out[pl + k];
+        float a_ux = __ldg(A.lu_out + k), a_uy = __ldg(A.lu_out + pl + k);
+        float a_mphx = __ldg(A.lm_out + k), a_mphy = __ldg(A.lm_out + pl + k);
         float a_upx = 0.f, a_upy = 0.f, a_mpx = 0.f, a_mpy = 0.f;
         float a_Fx = 0.f, a_Fy = 0.f, a_rho = 0.f, a_mu = 0.f, a_grx = 0.f, a_gry = 0.f, a_s1 = 0.f;
 
         // ---------------- flow collision (Eqs. (21)-(24)) reversed
         float lg[9];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) lg[i] = A.lg_out[(size_t)(i - 1) * pl + k];
+        for (int i = 1; i < 9; ++i) lg[i] = __ldg(A.lg_out + (size_t)(i - 1) * pl + k);
         const float a_m1 = 0.5f * (lg[1] - lg[3]);
         const float a_m2 = 0.5f * (lg[2] - lg[4]);
         const float a_m3 = 0.5f * (lg[1] + lg[3]);
@@ -354,7 +357,7 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
         for (int p = 0; p < NS; ++p) {
             float lf[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) lf[i] = A.lf_out[((size_t)p * 9 + i) * pl + k];
+            for (int i = 0; i < 9; ++i) lf[i] = __ldg(A.lf_out + ((size_t)p * 9 + i) * pl + k);
             const float phi = ph[p];
             const float Gx = 3.f * (phi * ux - php[p] * upx) + Rx[p];
             const float Gy = 3.f * (phi * uy - php[p] * upy) + Ry[p];
@@ -494,9 +497,9 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
         A.lm_in[k] = a_mpx;
         A.lm_in[pl + k] = a_mpy;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) A.gacc[(size_t)q * pl + k] += (double)dsig[q];
+        for (int q = 0; q < NP; ++q) A.gacc[(size_t)q * pl + k] = gacc[q] + (double)dsig[q];
         // s1 = 1 / (1/2 + 3 M): d s1 / dM = -3 s1^2
-        A.gacc[(size_t)NP * pl + k] += (double)(-3.f * s1 * s1 * a_s1);
+        A.gacc[(size_t)NP * pl + k] = gacc[NP] + (double)(-3.f * s1 * s1 * a_s1);
     }
 }
 
@@ -517,32 +520,37 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
-            a_w += 3.f * wgt(i) * (0.5f * aCy[i] * A.lF[n] - 0.5f * aCx[i] * A.lF[pl + n]);
+            a_w += 3.f * wgt(i) * (0.5f * aCy[i] * __ldg(A.lF + n) - 0.5f * aCx[i] * __ldg(A.lF + pl + n));
         }
-        const float upx = P.uin[k], upy = P.uin[pl + k];
-        const float mphx = T.mphi[k], mphy = T.mphi[pl + k];
+        const float upx = __ldg(P.uin + k), upy = __ldg(P.uin + pl + k);
+        const float mphx = __ldg(T.mphi + k), mphy = __ldg(T.mphi + pl + k);
         // w = mx uy - ux my (previous velocity)
-        const float a_mx = A.lmphi[k] + a_w * upy;
-        const float a_my = A.lmphi[pl + k] - a_w * upx;
-        A.lu_in[k] += -a_w * mphy;
-        A.lu_in[pl + k] += a_w * mphx;
+        const float a_mx = __ldg(A.lmphi + k) + a_w * upy;
+        const float a_my = __ldg(A.lmphi + pl + k) - a_w * upx;
+        // the values this pass updates, loaded before its first store (the
+        // compiler may not move a load across a store to another field)
+        const float lux = A.lu_in[k], luy = A.lu_in[pl + k];
+        const double gM = A.gacc[(size_t)NP * pl + k];
+        float pw[NS];
+#pragma unroll
+        for (int p = 0; p < NS; ++p) pw[p] = A.lphi_pw[(size_t)p * pl + k];
         // m_phi = -M sum_p drho_p (grad phi_p - R_p)
         float ph[N], gx[N], gy[N], a_ph[N], a_gx[N], a_gy[N], a_Rx[NS], a_Ry[NS];
         float sph = 0.f, sgx = 0.f, sgy = 0.f, dM = 0.f;
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
-            ph[p] = T.phi[(size_t)p * pl + k];
-            gx[p] = T.grad[(size_t)(2 * p) * pl + k];
-            gy[p] = T.grad[(size_t)(2 * p + 1) * pl + k];
+            ph[p] = __ldg(T.phi + (size_t)p * pl + k);
+            gx[p] = __ldg(T.grad + (size_t)(2 * p) * pl + k);
+            gy[p] = __ldg(T.grad + (size_t)(2 * p + 1) * pl + k);
             sph += ph[p];
             sgx += gx[p];
             sgy += gy[p];
             a_ph[p] = 0.f;
             a_gx[p] = A.lgrad[(size_t)(2 * p) * pl + k] - P.mob * P.drho[p] * a_mx;
             a_gy[p] = A.lgrad[(size_t)(2 * p + 1) * pl + k] - P.mob * P.drho[p] * a_my;
-            a_Rx[p] = A.lR[(size_t)(2 * p) * pl + k] + P.mob * P.drho[p] * a_mx;
-            a_Ry[p] = A.lR[(size_t)(2 * p + 1) * pl + k] + P.mob * P.drho[p] * a_my;
-            const float Rx = T.R[(size_t)(2 * p) * pl + k], Ry = T.R[(size_t)(2 * p + 1) * pl + k];
+            a_Rx[p] = __ldg(A.lR + (size_t)(2 * p) * pl + k) + P.mob * P.drho[p] * a_mx;
+            a_Ry[p] = __ldg(A.lR + (size_t)(2 * p + 1) * pl + k) + P.mob * P.drho[p] * a_my;
+            const float Rx = __ldg(T.R + (size_t)(2 * p) * pl + k), Ry = __ldg(T.R + (size_t)(2 * p + 1) * pl + k);
             dM -= P.drho[p] * ((gx[p] - Rx) * a_mx + (gy[p] - Ry) * a_my);
         }
         ph[NS] = 1.f - sph;
@@ -579,11 +587,13 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
             }
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
-            A.lphi_pw[(size_t)p * pl + k] += a_ph[p] - a_ph[NS];
+            A.lphi_pw[(size_t)p * pl + k] = pw[p] + (a_ph[p] - a_ph[NS]);
             A.lgrad[(size_t)(2 * p) * pl + k] = a_gx[p] - a_gx[NS];
             A.lgrad[(size_t)(2 * p + 1) * pl + k] = a_gy[p] - a_gy[NS];
         }
-        A.gacc[(size_t)NP * pl + k] += (double)dM;
+        A.lu_in[k] = lux + -a_w * mphy;
+        A.lu_in[pl + k] = luy + a_w * mphx;
+        A.gacc[(size_t)NP * pl + k] = gM + (double)dM;
     }
 }
 
@@ -601,11 +611,11 @@ __device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjF
         for (int p = 0; p < NS; ++p) {
             const float *lgx = A.lgrad + (size_t)(2 * p) * pl, *lgy = A.lgrad + (size_t)(2 * p + 1) * pl;
             const float *ll = A.llap + (size_t)p * pl;
-            float a = A.lphi_pw[(size_t)p * pl + k] - 6.f * (1.f - 4.f / 9.f) * ll[k];
+            float a = __ldg(A.lphi_pw + (size_t)p * pl + k) - 6.f * (1.f - 4.f / 9.f) * __ldg(ll + k);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
-                a += 3.f * wgt(i) * (aCx[i] * lgx[n] + aCy[i] * lgy[n]) + 6.f * wgt(i) * ll[n];
+                a += 3.f * wgt(i) * (aCx[i] * __ldg(lgx + n) + aCy[i] * __ldg(lgy + n)) + 6.f * wgt(i) * __ldg(ll + n);
             }
             A.lphi_tot[(size_t)p * pl + k] = a;
         }
@@ -627,10 +637,10 @@ __device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFiel
             const unsigned n = wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny);
 #pragma unroll
             for (int p = 0; p < NS; ++p)
-                A.lf_in[((size_t)p * 9 + i) * pl + k] = A.lphi_tot[(size_t)p * pl + n] +
-                                                        aCx[i] * A.lj[(size_t)(2 * p) * pl + n] +
-                                                        aCy[i] * A.lj[(size_t)(2 * p + 1) * pl + n];
-            if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = A.lg_pull[(size_t)(i - 1) * pl + n];
+                A.lf_in[((size_t)p * 9 + i) * pl + k] = __ldg(A.lphi_tot + (size_t)p * pl + n) +
+                                                        aCx[i] * __ldg(A.lj + (size_t)(2 * p) * pl + n) +
+                                                        aCy[i] * __ldg(A.lj + (size_t)(2 * p + 1) * pl + n);
+            if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = __ldg(A.lg_pull + (size_t)(i - 1) * pl + n);
         }
     }
 }

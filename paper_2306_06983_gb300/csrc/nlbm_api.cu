@@ -538,6 +538,68 @@ nlbm_status nlbm_get_tile(const nlbm_sim *s, int32_t *tx, int32_t *ty)
     return NLBM_OK;
 }
 
+nlbm_status nlbm_autotune(nlbm_sim *s, void *dev_scratch, size_t scratch_bytes, int32_t steps_per_trial,
+                          int32_t *best_tx, int32_t *best_ty, float *best_ms_per_step)
+{
+    if (!s || !dev_scratch || steps_per_trial < 1) return NLBM_EINVAL;
+    const size_t need = state_payload(s) + 16;
+    if (scratch_bytes < need) {
+        set_err(s->err, "scratch of %zu bytes is smaller than the %zu of state", scratch_bytes, need);
+        return NLBM_ENOMEM;
+    }
+    nlbm_status st = nlbm_save(s, dev_scratch);
+    if (st != NLBM_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(s, e, "timing events");
+    }
+    static const int kTx[] = {64, 128, 256};
+    static const int kTy[] = {0, 8, 12, 16, 20, 24, 32, 48};
+    float best = 1e30f;
+    int btx = s->tx, bty = s->ty;
+    for (int tx : kTx) {
+        // a strip of tx - 4 columns; skip widths the lattice cannot fill
+        if (tx > 64 && (tx / 2 - 4) >= s->kp.nx) continue;
+        for (int ty : kTy) {
+            s->tx = tx;
+            s->ty = ty;
+            for (int k = 0; k <= steps_per_trial && st == NLBM_OK; ++k) {
+                if (k == 1 && (e = cudaEventRecord(e0, s->stream)) != cudaSuccess) st = cuda_fail(s, e, "event");
+                StepParams kp = step_params(s, s->cur, s->cur ^ 1);
+                if (!s->half()) kp.pout = nullptr;
+                if (st == NLBM_OK && (e = launch_step(s, kp)) != cudaSuccess) st = cuda_fail(s, e, "trial step");
+                s->launches++;
+                s->cur ^= 1;
+            }
+            float ms = 0.f;
+            if (st == NLBM_OK &&
+                ((e = cudaEventRecord(e1, s->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                 (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess))
+                st = cuda_fail(s, e, "trial timing");
+            if (st != NLBM_OK) break;
+            ms /= steps_per_trial;
+            if (ms < best) {
+                best = ms;
+                btx = tx;
+                bty = ty;
+            }
+            if ((st = nlbm_restore(s, dev_scratch)) != NLBM_OK) break;
+        }
+        if (st != NLBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->tx = btx;
+    s->ty = bty;
+    if (st != NLBM_OK) return st;
+    if (best_tx) *best_tx = btx;
+    if (best_ty) *best_ty = bty;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return NLBM_OK;
+}
+
 void nlbm_destroy(nlbm_sim *s) { delete s; }
 
 }  // extern "C"

@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH):
         "nlbm_kernel_launches": (ctypes.c_int64, [vp]),
         "nlbm_set_tile": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
         "nlbm_get_tile": (st, [vp, P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "nlbm_autotune": (st, [vp, vp, ctypes.c_size_t, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                               P(ctypes.c_float)]),
         "nlbm_destroy": (None, [vp]),
         "nlbm_last_error": (ctypes.c_char_p, [vp]),
         "nlbm_status_string": (ctypes.c_char_p, [st]),
@@ -262,6 +264,13 @@ def nlbm_get_tile(h):
     return tx.value, ty.value
 
 
+def nlbm_autotune(h, scratch_ptr: int, scratch_bytes: int, steps_per_trial: int):
+    tx, ty, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load_library().nlbm_autotune(h, ctypes.c_void_p(scratch_ptr), scratch_bytes, steps_per_trial,
+                                        ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(ms)), h)
+    return tx.value, ty.value, ms.value
+
+
 def nlbm_destroy(h):
     load_library().nlbm_destroy(h)
 
@@ -398,6 +407,14 @@ class Simulation:
 
     def get_tile(self):
         return nlbm_get_tile(self.h)
+
+    def autotune(self, steps_per_trial: int = 20):
+        """Time every tile shape from the current state and keep the
+        fastest; returns (tx, ty, ms per step).  State and step count are
+        unchanged."""
+        n = nlbm_state_bytes(self.h)
+        scratch = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        return nlbm_autotune(self.h, scratch.data_ptr(), n, steps_per_trial)
 
 
 # ------------------------------------------------------------ ensembles

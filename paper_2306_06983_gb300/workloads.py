@@ -267,11 +267,13 @@ def lens_ensemble(count=64, seed=SEED, sizes=LENS_SIZES):
 
 def adjoint_problem(nx=256, ny=256, seed=SEED, sigma=(0.01, 0.01, 0.01), unit_delta=1e-3):
     """Three-phase, Model B, periodic problem of the gradient studies: disks
-    of phases 2 and 3 (seeded positions, radii U[nx/16, nx/8] but at least
-    1.5 eps) in phase 1; densities 1, relaxation time 1, mobility 0.1,
-    eps = 4; sigma = (sigma_12, sigma_13, sigma_23); unit vectors in the
-    smooth reading with delta = unit_delta (differentiable)."""
-    rmin, rmax = max(6.0, nx / 16.0), max(7.0, nx / 8.0)
+    of phases 2 and 3 (seeded positions, radii U[s/16, s/8], s = min(nx,
+    256), but at least 1.5 eps; 8 disks per 256^2 nodes) in phase 1;
+    densities 1, relaxation time 1, mobility 0.1, eps = 4; sigma = (sigma_12,
+    sigma_13, sigma_23); unit vectors in the smooth reading with delta =
+    unit_delta (differentiable)."""
+    s = min(nx, 256)
+    rmin, rmax = max(6.0, s / 16.0), max(7.0, s / 8.0)
     n_disks = max(2, int(round(8 * nx * ny / 256 ** 2)))
     p, phi0 = random_disks(nx, ny, 3, n_disks, rmin, rmax, seed=seed, model="B")
     s12, s13, s23 = sigma

@@ -351,3 +351,27 @@ def test_full_size_disks_2048():
     assert np.all(np.abs(m200 - m0) / np.abs(m0) < 1e-6)
     assert np.isfinite(phi200).all() and phi200.min() > -0.05 and phi200.max() < 1.05
     assert np.abs(u200).max() < 0.05
+
+
+def test_autotune_keeps_state_and_results():
+    """nlbm_autotune times every tile shape from a saved state and restores
+    it: the state, the step count and the later steps are those of a run
+    that never tuned (bitwise), and the kept shape is one of the trials."""
+    from paper_2306_06983_gb300.nlbm import Simulation
+    p, phi0 = W.random_smooth(200, 71, 5, seed=12, model="B", wall_y=True)
+    phi0 = f32(phi0)
+    a, b = Simulation(p), Simulation(p)
+    for s in (a, b):
+        s.set_phi(phi0)
+        s.step(7)
+    l0 = b.kernel_launches
+    tx, ty, ms = b.autotune(2)
+    assert (tx, ty) == b.get_tile() and tx in (64, 128, 256) and ty in (0, 8, 12, 16, 20, 24, 32, 48)
+    assert ms > 0 and b.kernel_launches > l0 and b.steps_done == a.steps_done == 7
+    for s in (a, b):
+        s.step(5)
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+    np.testing.assert_array_equal(a.phase_mass(), b.phase_mass())
+    a.close()
+    b.close()
