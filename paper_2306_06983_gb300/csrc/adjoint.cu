@@ -737,7 +737,11 @@ cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFiel
     }
     // the four passes overlap each launch with the drain of the one before
     // (measured: one cooperative launch with grid barriers between the
-    // passes is slower, 17.2 against 14.8 ms for the 256^2 sweep)
+    // passes is slower, 17.2 against 14.8 ms for the 256^2 sweep; passes 2-4
+    // as one launch over tiles of 32 x 8 nodes, pass 2 recomputed on a
+    // margin of two and pass 3 on a margin of one in shared memory, give
+    // 13.42 against 13.70 ms at 256^2 but 141.9 against 128.9 ms at 1024^2,
+    // and 32 x 16, 64 x 8, 32 x 32 tiles are slower at 1024^2 as well)
     cudaError_t e;
     if ((e = launch_pdl(rev_collide_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
     if ((e = launch_pdl(rev_source_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
