@@ -61,6 +61,29 @@ def bytes_per_lup(N: int, storage: str = "f32") -> int:
     return 2 * (2 * (8 * (N - 1) + 8) + 4 * (N - 1) + 4 * ((N - 1) + 5))
 
 
+def adjoint_bytes_per_lup(N: int) -> dict:
+    """Algorithmic HBM bytes of one differentiated lattice update (Model B,
+    FP32; NS = N - 1 solved phases, NP = N(N-1)/2 tension pairs), each field
+    a pass reads or writes counted once per pass:
+    forward step 8(10N + 2); reverse step = the taping rebuild (a forward
+    step that also writes 8 NS + 13 tape floats) and four passes:
+    1 collision: 8 NS + 12 tape, NS + 4 state and 10 NS + 12 seed floats
+      read, 9 NS + 16 adjoint floats written, NP + 1 FP64 sums updated;
+    2 source: 10 NS + 10 floats read, 3 NS + 2 written, one FP64 sum updated;
+    3 stencil: 4 NS read, NS written;
+    4 pull: 3 NS + 8 read, 9 NS + 8 written."""
+    NS, NP = N - 1, N * (N - 1) // 2
+    fwd = 8 * (10 * N + 2)
+    tape = fwd + 4 * (8 * NS + 13)
+    collide = 4 * ((8 * NS + 12) + (NS + 4) + (10 * NS + 12) + (9 * NS + 16)) + 16 * (NP + 1)
+    source = 4 * ((10 * NS + 10) + (3 * NS + 2)) + 16
+    stencil = 4 * (4 * NS + NS)
+    pull = 4 * ((3 * NS + 8) + (9 * NS + 8))
+    return {"forward": fwd, "reverse": tape + collide + source + stencil + pull,
+            "reverse_parts": {"taping_rebuild": tape, "collision": collide, "source": source,
+                              "stencil": stencil, "pull": pull}}
+
+
 def kernel_sources_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_06983_gb300", "csrc")
@@ -336,7 +359,8 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         del sims
         torch.cuda.empty_cache()
         forms["rti"] = measure_rti(args, timed, stream, peak)
-        forms["adjoint"] = measure_adjoint(timed)
+        forms["adjoint"] = measure_adjoint(timed, 256, peak)
+        forms["adjoint_1024"] = measure_adjoint(timed, 1024, peak)
     return forms
 
 
@@ -428,7 +452,7 @@ def measure_rti(args, timed, stream, peak):
     }
 
 
-def measure_adjoint(timed, n=256):
+def measure_adjoint(timed, n=256, peak=None):
     """Gradient study (n x n periodic, 256 by default, N = 3, Model B, 500 steps, a
     checkpoint every 50, smooth unit vectors delta = 1e-3): L = 1/2 |phi(T) -
     phi_hat|^2 with phi_hat from sigma = (0.012, 0.008, 0.010); gradients with
@@ -487,6 +511,17 @@ def measure_adjoint(timed, n=256):
     run.close()
     fwd, bwd = float(np.median(fwds)), float(np.median(bwds))
     nodes = n * n
+    ab = adjoint_bytes_per_lup(N)
+    roof = None
+    if peak:
+        gbs = (ab["forward"] + ab["reverse"]) * nodes * T / ((fwd + bwd) / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "algorithmic_bytes_per_lup": ab,
+                "forward_frac": round(ab["forward"] * nodes * T / (fwd / 1e3) / 1e9 / peak, 4),
+                "backward_frac": round(ab["reverse"] * nodes * T / (bwd / 1e3) / 1e9 / peak, 4),
+                "note": ("the step's fields (%.0f MB) fit the 129 MB L2: bound by launch and dependency latency, "
+                         "not by HBM" % (nodes * 4 * (10 * N + 2) / 1e6)) if nodes * 4 * (10 * N + 2) < 129e6
+                else "fields larger than L2"}
     return {
         "workload": f"{n}x{n} periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
                     "v/sqrt(|v|^2+1e-6); L2 mismatch of phi(T) against the sigma=(0.012,0.008,0.010) run",
@@ -497,6 +532,7 @@ def measure_adjoint(timed, n=256):
         "loss": float(0.5 * ((phiT.double() - tgt.double()) ** 2).sum()),
         "grad_sigma_pairs": [float(gs[a, b]) for a, b in pair_list(N)], "grad_mobility": float(gm),
         "grad_phi0_max_abs": float(g0.abs().max()),
+        "roofline": roof,
     }
 
 
@@ -537,7 +573,8 @@ def run_adjoint_only(args):
         e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1) / steps
-    print(json.dumps({"metric": METRIC, "forms": {"adjoint": measure_adjoint(timed, args.only_adjoint)}}),
+    peak, _ = peak_hbm()
+    print(json.dumps({"metric": METRIC, "forms": {"adjoint": measure_adjoint(timed, args.only_adjoint, peak)}}),
           flush=True)
 
 
