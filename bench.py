@@ -361,6 +361,7 @@ def measure_forms(args, p, phi0, ref_fields, lups, peak):
         forms["rti"] = measure_rti(args, timed, stream, peak)
         forms["adjoint"] = measure_adjoint(timed, 256, peak)
         forms["adjoint_1024"] = measure_adjoint(timed, 1024, peak)
+        forms["adjoint_model_A"] = measure_adjoint(timed, 256, peak, model="A")
     return forms
 
 
@@ -452,8 +453,9 @@ def measure_rti(args, timed, stream, peak):
     }
 
 
-def measure_adjoint(timed, n=256, peak=None):
-    """Gradient study (n x n periodic, 256 by default, N = 3, Model B, 500 steps, a
+def measure_adjoint(timed, n=256, peak=None, model="B"):
+    """Gradient study (n x n periodic, 256 by default, N = 3, Model B or A with
+    n = 1, 500 steps, a
     checkpoint every 50, smooth unit vectors delta = 1e-3): L = 1/2 |phi(T) -
     phi_hat|^2 with phi_hat from sigma = (0.012, 0.008, 0.010); gradients with
     respect to the three tensions, the mobility and the initial fields from
@@ -465,6 +467,7 @@ def measure_adjoint(timed, n=256, peak=None):
     from paper_2306_06983_gb300.nlbm import AdjointRun, Simulation, pair_list
     T, every = 500, 50
     p, phi0 = W.adjoint_problem(n, n)
+    p = dict(p, model=model, model_a_n=1.0)
     phi0 = phi0.astype(np.float32)
     N = p["n_phases"]
 
@@ -523,7 +526,8 @@ def measure_adjoint(timed, n=256, peak=None):
                          "not by HBM" % (nodes * 4 * (10 * N + 2) / 1e6)) if nodes * 4 * (10 * N + 2) < 129e6
                 else "fields larger than L2"}
     return {
-        "workload": f"{n}x{n} periodic N=3 Model B disks, 500 steps, checkpoint every 50, unit vectors "
+        "workload": f"{n}x{n} periodic N=3 Model {model}{' (n = 1)' if model == 'A' else ''} disks, 500 steps, "
+                    "checkpoint every 50, unit vectors "
                     "v/sqrt(|v|^2+1e-6); L2 mismatch of phi(T) against the sigma=(0.012,0.008,0.010) run",
         "value": round(nodes * T / ((fwd + bwd) / 1e3) / 1e6, 2), "unit": "MLUPS (differentiated)",
         "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3), "backward_over_forward": round(bwd / fwd, 2),

@@ -1,4 +1,4 @@
-// Reverse (adjoint) of the fused step, Model B, periodic lattice, FP32.
+// Reverse (adjoint) of the fused step, Models A and B, periodic lattice, FP32.
 //
 // For a loss L(phi(T)) the adjoint runs the steps backwards.  For each step t
 // it first rebuilds the step's intermediate fields from the step's input
@@ -9,7 +9,8 @@
 //         relations (Eqs. (25b), (25c), (13)), the mixture rules (Eqs. (11),
 //         (12)) and F_s with the chemical potentials (Eqs. (16), (17));
 //   rev2  transpose of F_c's stencil (gather of the F adjoint), then w,
-//         m_phi (Eq. (13)) and the Model B source (Eqs. (3), (4)) pointwise;
+//         m_phi (Eq. (13)) and the source (Model A, Eq. (2); Model B,
+//         Eqs. (3), (4)) pointwise;
 //   rev3  transposes of the isotropic gradient and Laplacian (Eq. (27));
 //   rev4  transpose of the pull (streaming) and of the moments
 //         phi = sum f_i, j = sum c_i f_i (Eq. (25a)).
@@ -35,6 +36,37 @@ __device__ __forceinline__ unsigned wrap_node(int x, int y, int nx, int ny)
     x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
     y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
     return (unsigned)y * nx + x;
+}
+
+// Model A's weight w(phi) = max(phi, 0)^n (Eq. (2)) and dw/dphi
+// (n max(phi, 0)^(n-1); 0 where phi <= 0).  Integer n in 1..8 by
+// multiplication, as in the forward kernel.
+__device__ __forceinline__ float wa(const StepParams &P, float ph)
+{
+    const float pc = fmaxf(ph, 0.f);
+    if (P.model_n_int > 0) {
+        float w = pc;
+        for (int k = 1; k < P.model_n_int; ++k) w *= pc;
+        return w;
+    }
+    return pc > 0.f ? powf(pc, P.model_n) : 0.f;
+}
+__device__ __forceinline__ float dwa(const StepParams &P, float ph)
+{
+    if (!(ph > 0.f)) return 0.f;
+    if (P.model_n_int > 0) {
+        float w = 1.f;
+        for (int k = 1; k < P.model_n_int; ++k) w *= ph;
+        return (float)P.model_n_int * w;
+    }
+    return P.model_n * powf(ph, P.model_n - 1.f);
+}
+
+// 1 / |v| of a unit vector n = v / |v|: smooth reading 1 / sqrt(|v|^2 +
+// delta^2), else 1 / |v| with n = 0 (returned 0) below the threshold.
+__device__ __forceinline__ float unit_r(const StepParams &P, float n2)
+{
+    return P.unit_delta2 > 0.f ? rsqrtf(n2 + P.unit_delta2) : (n2 > 1e-24f ? rsqrtf(n2) : 0.f);
 }
 
 // g'(s) = 2 s (1 - s) (1 - 2 s) and its derivative (Eq. (17)).
@@ -70,10 +102,10 @@ __global__ void tape_pull_kernel(const StepParams P, AdjTape T)
     }
 }
 
-// grad phi and lap phi (Eq. (27)) of phases 1..N-1, the Model B source
-// (Eqs. (3), (4)), m_phi (Eq. (13)) and w = m_phi,x u_y - u_x m_phi,y with
-// the previous velocity.
-template <int NS>
+// grad phi and lap phi (Eq. (27)) of phases 1..N-1, the source (Model A,
+// Eq. (2); Model B, Eqs. (3), (4)), m_phi (Eq. (13)) and w = m_phi,x u_y -
+// u_x m_phi,y with the previous velocity.
+template <int NS, int MODEL>
 __global__ void tape_stencil_kernel(const StepParams P, AdjTape T)
 {
     constexpr int N = NS + 1;
@@ -110,17 +142,36 @@ __global__ void tape_stencil_kernel(const StepParams P, AdjTape T)
         float Rx[NS], Ry[NS];
 #pragma unroll
         for (int p = 0; p < NS; ++p) Rx[p] = Ry[p] = 0.f;
+        if constexpr (MODEL == 0) {
+            // R_p = a_p n_p - w_p / (sum_q w_q) sum_q a_q n_q, a_q = 4 phi_q (1 - phi_q) / eps
+            float ax[N], ay[N], S = 0.f, Vx = 0.f, Vy = 0.f;
 #pragma unroll
-        for (int p = 0; p < N; ++p)
-#pragma unroll
-            for (int q = p + 1; q < N; ++q) {
-                const float vx = ph[q] * gx[p] - ph[p] * gx[q], vy = ph[q] * gy[p] - ph[p] * gy[q];
-                const float n2 = vx * vx + vy * vy;
-                const float r = P.unit_delta2 > 0.f ? rsqrtf(n2 + P.unit_delta2) : (n2 > 1e-24f ? rsqrtf(n2) : 0.f);
-                const float c = P.four_over_eps * ph[p] * ph[q] * r;
-                if (p < NS) { Rx[p] += c * vx; Ry[p] += c * vy; }
-                if (q < NS) { Rx[q] -= c * vx; Ry[q] -= c * vy; }
+            for (int q = 0; q < N; ++q) {
+                const float ar = P.four_over_eps * ph[q] * (1.f - ph[q]) * unit_r(P, gx[q] * gx[q] + gy[q] * gy[q]);
+                ax[q] = ar * gx[q];
+                ay[q] = ar * gy[q];
+                S += wa(P, ph[q]);
+                Vx += ax[q];
+                Vy += ay[q];
             }
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+                const float b = wa(P, ph[p]) / S;
+                Rx[p] = ax[p] - b * Vx;
+                Ry[p] = ay[p] - b * Vy;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < N; ++p)
+#pragma unroll
+                for (int q = p + 1; q < N; ++q) {
+                    const float vx = ph[q] * gx[p] - ph[p] * gx[q], vy = ph[q] * gy[p] - ph[p] * gy[q];
+                    const float r = unit_r(P, vx * vx + vy * vy);
+                    const float c = P.four_over_eps * ph[p] * ph[q] * r;
+                    if (p < NS) { Rx[p] += c * vx; Ry[p] += c * vy; }
+                    if (q < NS) { Rx[q] -= c * vx; Ry[q] -= c * vy; }
+                }
+        }
         float mx = 0.f, my = 0.f;
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -505,8 +556,8 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
 
 
 // rev2: F_c's stencil transposed (gather of the F adjoint at the
-// neighbours), then w, m_phi and the Model B source at the node.
-template <int NS>
+// neighbours), then w, m_phi and the source (Model A or B) at the node.
+template <int NS, int MODEL>
 __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTape &T, const AdjFields &A, unsigned k)
 {
     constexpr int N = NS + 1;
@@ -557,6 +608,49 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
         gx[NS] = -sgx;
         gy[NS] = -sgy;
         a_ph[NS] = a_gx[NS] = a_gy[NS] = 0.f;
+        if constexpr (MODEL == 0) {
+            // Model A source: R_p = A_p - beta_p V with A_q = a_q n_q, a_q =
+            // 4 phi_q (1 - phi_q) / eps, n_q = grad phi_q / s_q, V = sum_q A_q
+            // (all N phases), beta_p = w_p / S, w_q = max(phi_q, 0)^n, S =
+            // sum_q w_q.  Adjoints: the A-adjoint of phase q is its R-adjoint
+            // (0 for phase N) minus sum_p beta_p (R-adjoint of p); the
+            // w-adjoint is (b_q - sum_p b_p beta_p) / S with b_p = -(R-adjoint
+            // of p) . V; a_q's and n_q's parts as in Model B ((I - n n^T) / s).
+            float nxq[N], nyq[N], rq[N], aq[N], w[N];
+            float S = 0.f, Vx = 0.f, Vy = 0.f;
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                aq[q] = P.four_over_eps * ph[q] * (1.f - ph[q]);
+                rq[q] = unit_r(P, gx[q] * gx[q] + gy[q] * gy[q]);
+                nxq[q] = gx[q] * rq[q];
+                nyq[q] = gy[q] * rq[q];
+                w[q] = wa(P, ph[q]);
+                S += w[q];
+                Vx += aq[q] * nxq[q];
+                Vy += aq[q] * nyq[q];
+            }
+            const float invS = 1.f / S;
+            float gbx = 0.f, gby = 0.f, bb = 0.f, b[N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const float rx = q < NS ? a_Rx[q] : 0.f, ry = q < NS ? a_Ry[q] : 0.f;
+                const float beta = w[q] * invS;
+                gbx -= beta * rx;
+                gby -= beta * ry;
+                b[q] = -(rx * Vx + ry * Vy);
+                bb += b[q] * beta;
+            }
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const float Ax = (q < NS ? a_Rx[q] : 0.f) + gbx, Ay = (q < NS ? a_Ry[q] : 0.f) + gby;
+                a_ph[q] += (b[q] - bb) * invS * dwa(P, ph[q]);
+                if (rq[q] == 0.f) continue;   // n = 0 below the threshold (thresholded reading)
+                const float an = Ax * nxq[q] + Ay * nyq[q];
+                a_ph[q] += an * P.four_over_eps * (1.f - 2.f * ph[q]);
+                a_gx[q] += aq[q] * (Ax - an * nxq[q]) * rq[q];
+                a_gy[q] += aq[q] * (Ay - an * nyq[q]) * rq[q];
+            }
+        } else {
         // Model B source: pair (p, q) adds T = (4/eps) phi_p phi_q n_pq to R_p
         // and subtracts it from R_q, n_pq = unit(phi_q grad phi_p - phi_p grad phi_q)
 #pragma unroll
@@ -585,6 +679,7 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
                 a_gx[q] -= ph[p] * avx;
                 a_gy[q] -= ph[p] * avy;
             }
+        }
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
             A.lphi_pw[(size_t)p * pl + k] = pw[p] + (a_ph[p] - a_ph[NS]);
@@ -656,12 +751,12 @@ __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
         rev_collide_node<NS>(P, T, A, k);
 }
 
-template <int NS>
+template <int NS, int MODEL>
 __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
 {
     pdl_wait();
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
-        rev_source_node<NS>(P, T, A, k);
+        rev_source_node<NS, MODEL>(P, T, A, k);
 }
 
 template <int NS>
@@ -725,14 +820,14 @@ int blocks_for(unsigned n)
 // 12.7 ms for 40 steps).
 constexpr int kRevThreads = 256;
 
-template <int NS>
+template <int NS, int MODEL>
 cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped, cudaStream_t st)
 {
     const int nb = blocks_for(P.plane);
     const int nr = (int)((P.plane + kRevThreads - 1) / kRevThreads);
     if (!taped) {
         tape_pull_kernel<NS><<<nb, 256, 0, st>>>(P, T);
-        tape_stencil_kernel<NS><<<nb, 256, 0, st>>>(P, T);
+        tape_stencil_kernel<NS, MODEL><<<nb, 256, 0, st>>>(P, T);
         tape_force_kernel<NS><<<nb, 256, 0, st>>>(P, T);
     }
     // the four passes overlap each launch with the drain of the one before
@@ -744,7 +839,7 @@ cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFiel
     // and 32 x 16, 64 x 8, 32 x 32 tiles are slower at 1024^2 as well)
     cudaError_t e;
     if ((e = launch_pdl(rev_collide_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
-    if ((e = launch_pdl(rev_source_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_source_kernel<NS, MODEL>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
     if ((e = launch_pdl(rev_stencil_kernel<NS>, nr, kRevThreads, 0, st, P, A)) != cudaSuccess) return e;
     return launch_pdl(rev_pull_kernel<NS>, nr, kRevThreads, 0, st, P, A);
 }
@@ -770,7 +865,7 @@ cudaError_t launch_reverse_step(int ns, const StepParams &P, const AdjTape &T, c
 {
     switch (ns) {
 #define NLBM_CASE(K) \
-    case K: return reverse_step_ns<K>(P, T, A, taped, st);
+    case K: return P.model == 0 ? reverse_step_ns<K, 0>(P, T, A, taped, st) : reverse_step_ns<K, 1>(P, T, A, taped, st);
         NLBM_CASE(1) NLBM_CASE(2) NLBM_CASE(3) NLBM_CASE(4) NLBM_CASE(5) NLBM_CASE(6) NLBM_CASE(7)
 #undef NLBM_CASE
     default: return cudaErrorInvalidValue;

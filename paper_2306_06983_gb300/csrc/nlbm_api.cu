@@ -1102,9 +1102,9 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
 {
     nlbm_status st = validate(p, nullptr, err);
     if (st != NLBM_OK) return st;
-    if (p->model != NLBM_MODEL_B || p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC ||
-        p->storage != NLBM_STORE_F32 || p->gx != 0.0 || p->gy != 0.0) {
-        set_err(err, "the adjoint covers Model B on a periodic lattice with FP32 storage and no gravity");
+    if (p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC || p->storage != NLBM_STORE_F32 ||
+        p->gx != 0.0 || p->gy != 0.0) {
+        set_err(err, "the adjoint covers a periodic lattice with FP32 storage and no gravity");
         return NLBM_ENOTSUP;
     }
     if (nsteps < 1 || every < 1) { set_err(err, "nsteps and checkpoint interval must be >= 1"); return NLBM_EINVAL; }
@@ -1206,7 +1206,7 @@ AdjFields adj_fields(const nlbm_adjoint *a, float *so, float *si)
     return A;
 }
 
-// Tape k of the rebuilt segment (the field order of launch_step_tape_b_f32).
+// Tape k of the rebuilt segment (the field order of launch_step_tape_{a,b}_f32).
 AdjTape adj_tape(const nlbm_adjoint *a, int k)
 {
     const size_t pl = a->plane;
@@ -1267,7 +1267,9 @@ cudaError_t adj_backward_body(nlbm_adjoint *a)
             kp.mphi = kp.phi + pl * ns;   // read from the input state, written to the output
             kp.pout = nullptr;
             kp.tape = a->tapes + pl * (size_t)c.tape * (s - 1);
-            if ((e = launch_step_tape_b_f32(ns, kp, a->stream)) != cudaSuccess) return e;
+            if ((e = (kp.model == NLBM_MODEL_A ? launch_step_tape_a_f32 : launch_step_tape_b_f32)(ns, kp, a->stream)) !=
+                cudaSuccess)
+                return e;
         }
         for (int s = len - 1; s >= 0; --s) {
             const StepParams kp = adj_params_from_state(a, a->seg + a->state_floats * s);

@@ -122,10 +122,12 @@ cudaError_t launch_step_b_bf16(int ns, const StepParams &p, int tx, int ty, cuda
 cudaError_t launch_step_a_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 cudaError_t launch_step_b_f16(int ns, const StepParams &p, int tx, int ty, cudaStream_t st);
 
-// The FP32 Model B step (128-thread blocks) that also writes the step's
+// The FP32 step (128-thread blocks) that also writes the step's
 // intermediate fields for the adjoint to p.tape, 8 (N-1) + 13 planes in the
 // order of AdjTape: phi [N-1], j [2(N-1)], pulled g [8], grad phi [2(N-1)],
-// lap phi [N-1], R [2(N-1)], m_phi [2], w [1], F [2] (step_b_f32_tape.cu).
+// lap phi [N-1], R [2(N-1)], m_phi [2], w [1], F [2]; Model A in
+// step_a_f32_tape.cu, Model B in step_b_f32_tape.cu.
+cudaError_t launch_step_tape_a_f32(int ns, const StepParams &p, cudaStream_t st);
 cudaError_t launch_step_tape_b_f32(int ns, const StepParams &p, cudaStream_t st);
 
 // Ensemble of independent simulations (batch.cu): one persistent launch

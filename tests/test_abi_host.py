@@ -130,6 +130,18 @@ def test_adjoint_refuses_gravity(lib):
     assert ei.value.status == 4
 
 
+def test_adjoint_scope_models_and_boundaries(lib):
+    """Both models are accepted; walls and 16-bit storage are refused."""
+    from paper_2306_06983_gb300 import nlbm
+    p, _ = W.adjoint_problem(32, 32)
+    a = nlbm.nlbm_adjoint_workspace_bytes(dict(p, model="A", model_a_n=1.5), 10, 5)
+    assert a == nlbm.nlbm_adjoint_workspace_bytes(p, 10, 5)
+    for bad in (dict(p, wall_y=True), dict(p, wall_x=True), dict(p, storage="bf16")):
+        with pytest.raises(nlbm.NlbmError) as ei:
+            nlbm.nlbm_adjoint_workspace_bytes(bad, 10, 5)
+        assert ei.value.status == 4
+
+
 def test_sigma_must_be_symmetric_positive(lib):
     from paper_2306_06983_gb300 import nlbm
     p, _ = W.droplets_64("B")
