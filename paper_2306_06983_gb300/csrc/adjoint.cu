@@ -1,4 +1,5 @@
-// Reverse (adjoint) of the fused step, Models A and B, periodic lattice, FP32.
+// Reverse (adjoint) of the fused step, Models A and B, periodic lattice,
+// gravity, FP32.
 //
 // For a loss L(phi(T)) the adjoint runs the steps backwards.  For each step t
 // it first rebuilds the step's intermediate fields from the step's input
@@ -210,7 +211,7 @@ __device__ __forceinline__ void chem_pot(const StepParams &P, const float (&ph)[
         }
 }
 
-// F = F_s + F_c (Eq. (16) and the lagged-velocity F_c).
+// F = F_s + F_c + F_g (Eq. (16), the lagged-velocity F_c and gravity rho g).
 template <int NS>
 __global__ void tape_force_kernel(const StepParams P, AdjTape T)
 {
@@ -230,6 +231,9 @@ __global__ void tape_force_kernel(const StepParams P, AdjTape T)
         ph[NS] = 1.f - sph;
         lap[NS] = -sl;
         chem_pot<NS>(P, ph, lap, mu);
+        float rho = P.rhoN;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) rho += P.drho[p] * ph[p];
         float Fx = 0.f, Fy = 0.f;
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -244,8 +248,8 @@ __global__ void tape_force_kernel(const StepParams P, AdjTape T)
             dxw += 3.f * wgt(i) * aCx[i] * v;
             dyw += 3.f * wgt(i) * aCy[i] * v;
         }
-        T.F[k] = Fx + 0.5f * dyw;
-        T.F[pl + k] = Fy - 0.5f * dxw;
+        T.F[k] = Fx + 0.5f * dyw + rho * P.gx;
+        T.F[pl + k] = Fy - 0.5f * dxw + rho * P.gy;
     }
 }
 
@@ -484,6 +488,8 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
                                                   cy * cy * a_Pyy + cx * cy * a_Pxy;
         }
 
+        // ---------------- gravity F_g = rho g in the total force
+        a_rho += a_Fx * P.gx + a_Fy * P.gy;
         // ---------------- mixture rules (Eqs. (11), (12)) and F_s (Eqs. (16), (17))
 #pragma unroll
         for (int p = 0; p < NS; ++p) {

@@ -1102,9 +1102,8 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
 {
     nlbm_status st = validate(p, nullptr, err);
     if (st != NLBM_OK) return st;
-    if (p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC || p->storage != NLBM_STORE_F32 ||
-        p->gx != 0.0 || p->gy != 0.0) {
-        set_err(err, "the adjoint covers a periodic lattice with FP32 storage and no gravity");
+    if (p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC || p->storage != NLBM_STORE_F32) {
+        set_err(err, "the adjoint covers a periodic lattice with FP32 storage");
         return NLBM_ENOTSUP;
     }
     if (nsteps < 1 || every < 1) { set_err(err, "nsteps and checkpoint interval must be >= 1"); return NLBM_EINVAL; }

@@ -121,21 +121,14 @@ def test_gravity_and_wetting_walls_are_accepted(lib):
     assert nlbm.nlbm_workspace_bytes(q) == base
 
 
-def test_adjoint_refuses_gravity(lib):
-    from paper_2306_06983_gb300 import nlbm
-    p, _ = W.adjoint_problem(32, 32)
-    nlbm.nlbm_adjoint_workspace_bytes(p, 10, 5)
-    with pytest.raises(nlbm.NlbmError) as ei:
-        nlbm.nlbm_adjoint_workspace_bytes(dict(p, gy=1e-5), 10, 5)
-    assert ei.value.status == 4
-
-
 def test_adjoint_scope_models_and_boundaries(lib):
-    """Both models are accepted; walls and 16-bit storage are refused."""
+    """Both models and gravity are accepted; walls and 16-bit storage are
+    refused."""
     from paper_2306_06983_gb300 import nlbm
     p, _ = W.adjoint_problem(32, 32)
     a = nlbm.nlbm_adjoint_workspace_bytes(dict(p, model="A", model_a_n=1.5), 10, 5)
     assert a == nlbm.nlbm_adjoint_workspace_bytes(p, 10, 5)
+    assert a == nlbm.nlbm_adjoint_workspace_bytes(dict(p, gx=1e-5, gy=-2e-5), 10, 5)
     for bad in (dict(p, wall_y=True), dict(p, wall_x=True), dict(p, storage="bf16")):
         with pytest.raises(nlbm.NlbmError) as ei:
             nlbm.nlbm_adjoint_workspace_bytes(bad, 10, 5)
