@@ -337,8 +337,9 @@ const char *nlbm_batch_last_error(const nlbm_batch *b);
  * Eqs. (16), (25); the source, Model A Eq. (2) or Model B Eqs. (3)-(4); the
  * stencils, Eq. (27); streaming); states are checkpointed every
  * `checkpoint_every` steps and each segment is recomputed during the sweep.
- * Supported: Models A and B, periodic on both axes, FP32 storage, with or
- * without gravity (ENOTSUP otherwise: walls, 16-bit storage).  Model A's weight max(phi, 0)^n has the
+ * Supported: Models A and B, periodic axes or half-way bounce-back walls
+ * without wetting (all contact angles 90 degrees), gravity, FP32 storage
+ * (ENOTSUP otherwise: wetting walls, 16-bit storage).  Model A's weight max(phi, 0)^n has the
  * derivative n phi^(n-1) for phi > 0 and 0 below, so with n < 1 gradients
  * through nodes where a phase tends to 0+ are unbounded.  Unit vectors
  * should use the smooth reading (p->unit_delta > 0, e.g. 1e-3): with the

@@ -1,5 +1,5 @@
-// Reverse (adjoint) of the fused step, Models A and B, periodic lattice,
-// gravity, FP32.
+// Reverse (adjoint) of the fused step, Models A and B, periodic axes or
+// half-way bounce-back walls (without wetting), gravity, FP32.
 //
 // For a loss L(phi(T)) the adjoint runs the steps backwards.  For each step t
 // it first rebuilds the step's intermediate fields from the step's input
@@ -32,12 +32,63 @@ __constant__ int aCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 __device__ __forceinline__ float wgt(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
 
+__constant__ int aOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
 __device__ __forceinline__ unsigned wrap_node(int x, int y, int nx, int ny)
 {
     x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
     y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
     return (unsigned)y * nx + x;
 }
+
+// Boundaries (half-way bounce-back walls on x and/or y, periodic otherwise),
+// for positions at most one node outside the lattice.
+// Whether (x, y) lies beyond a wall.
+__device__ __forceinline__ bool beyond_wall(const StepParams &P, int x, int y)
+{
+    return (P.wall_x && (x < 0 || x >= P.nx)) || (P.wall_y && (y < 0 || y >= P.ny));
+}
+// The node a position stands for: periodic wrap, or the mirror image
+// across a wall (a ghost node, whose phi is that of its image); fx, fy
+// report mirroring across an x or a y wall.
+__device__ __forceinline__ unsigned image_node(const StepParams &P, int x, int y, bool &fx, bool &fy)
+{
+    fx = P.wall_x && (x < 0 || x >= P.nx);
+    fy = P.wall_y && (y < 0 || y >= P.ny);
+    x = x < 0 ? (fx ? -1 - x : x + P.nx) : (x >= P.nx ? (fx ? 2 * P.nx - 1 - x : x - P.nx) : x);
+    y = y < 0 ? (fy ? -1 - y : y + P.ny) : (y >= P.ny ? (fy ? 2 * P.ny - 1 - y : y - P.ny) : y);
+    return (unsigned)y * P.nx + x;
+}
+// The positions that stand for node (x, y): itself and the ghost nodes
+// beyond the walls it touches (up to 4 on a lattice one node wide with
+// walls on both axes); returns their number, the first being the node.
+__device__ __forceinline__ int standins(const StepParams &P, int x, int y, int (&px)[9], int (&py)[9])
+{
+    int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0}, nxs = 1, nys = 1;
+    if (P.wall_x) {
+        if (x == 0) xs[nxs++] = -1;
+        if (x == P.nx - 1) xs[nxs++] = P.nx;
+    }
+    if (P.wall_y) {
+        if (y == 0) ys[nys++] = -1;
+        if (y == P.ny - 1) ys[nys++] = P.ny;
+    }
+    int n = 0;
+    for (int b = 0; b < nys; ++b)
+        for (int a = 0; a < nxs; ++a) {
+            px[n] = xs[a];
+            py[n] = ys[b];
+            ++n;
+        }
+    return n;
+}
+// w = m_phi,x u_y - u_x m_phi,y at a ghost of a node, from the node's m_phi
+// and previous velocity: the ghost's m_phi is the mirror image (normal
+// component negated) and its velocity the no-slip ghost -u per mirroring,
+// so w = s1 m_x u_y + s2 u_x m_y with s1 = -1 across a y wall, s2 = +1
+// across an x wall (s1 = 1, s2 = -1 at the node itself).
+__device__ __forceinline__ float w_sign1(bool fx, bool fy) { (void)fx; return fy ? -1.f : 1.f; }
+__device__ __forceinline__ float w_sign2(bool fx, bool fy) { (void)fy; return fx ? 1.f : -1.f; }
 
 // Model A's weight w(phi) = max(phi, 0)^n (Eq. (2)) and dw/dphi
 // (n max(phi, 0)^(n-1); 0 where phi <= 0).  Integer n in 1..8 by
@@ -88,7 +139,10 @@ __global__ void tape_pull_kernel(const StepParams P, AdjTape T)
             float ph = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float f = P.fin[((size_t)p * 9 + i) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
+                // pulled from x - c_i, or bounced back at a wall (f*_opp(i) of the node)
+                const bool bb = beyond_wall(P, x - aCx[i], y - aCy[i]);
+                const float f = bb ? P.fin[((size_t)p * 9 + aOpp[i]) * pl + k]
+                                   : P.fin[((size_t)p * 9 + i) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
                 ph += f;
                 jx += aCx[i] * f;
                 jy += aCy[i] * f;
@@ -98,8 +152,11 @@ __global__ void tape_pull_kernel(const StepParams P, AdjTape T)
             T.j[(size_t)(2 * p + 1) * pl + k] = jy;
         }
 #pragma unroll
-        for (int i = 1; i < 9; ++i)
-            T.g[(size_t)(i - 1) * pl + k] = P.gin[(size_t)(i - 1) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
+        for (int i = 1; i < 9; ++i) {
+            const bool bb = beyond_wall(P, x - aCx[i], y - aCy[i]);
+            T.g[(size_t)(i - 1) * pl + k] = bb ? P.gin[(size_t)(aOpp[i] - 1) * pl + k]
+                                               : P.gin[(size_t)(i - 1) * pl + wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny)];
+        }
     }
 }
 
@@ -122,7 +179,8 @@ __global__ void tape_stencil_kernel(const StepParams P, AdjTape T)
             float ax = 0.f, ay = 0.f, lap = 0.f;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                const float v = f[wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny)];
+                bool fx, fy;
+                const float v = f[image_node(P, x + aCx[i], y + aCy[i], fx, fy)];
                 ax += 3.f * wgt(i) * aCx[i] * v;
                 ay += 3.f * wgt(i) * aCy[i] * v;
                 lap += 6.f * wgt(i) * (v - c);
@@ -244,7 +302,13 @@ __global__ void tape_force_kernel(const StepParams P, AdjTape T)
         float dxw = 0.f, dyw = 0.f;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const float v = T.w[wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny)];
+            bool fx, fy;
+            const unsigned n = image_node(P, x + aCx[i], y + aCy[i], fx, fy);
+            float v = T.w[n];
+            if (fx || fy) {
+                const float mx = T.mphi[n], my = T.mphi[pl + n], ux = P.uin[n], uy = P.uin[pl + n];
+                v = w_sign1(fx, fy) * mx * uy + w_sign2(fx, fy) * ux * my;
+            }
             dxw += 3.f * wgt(i) * aCx[i] * v;
             dyw += 3.f * wgt(i) * aCy[i] * v;
         }
@@ -571,19 +635,41 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
     const unsigned pl = P.plane;
     {
         const int x = k % P.nx, y = k / P.nx;
-        // F_c(x) = (1/2 d_y w, -1/2 d_x w): w(z) enters F_c(z - c_i) with
-        // weight 3 w_i c_i.
-        float a_w = 0.f;
+        // F_c(x) = (1/2 d_y w, -1/2 d_x w): w at position z enters F_c(z -
+        // c_i) with weight 3 w_i c_i; the positions holding this node's w
+        // are the node and, next to a wall, its ghosts (w there formed from
+        // this node's m_phi and u with the signs s1, s2 of w_sign1/2).
+        float a_w = 0.f, a_ws1 = 0.f, a_ws2 = 0.f;
+        if (!P.wall_x && !P.wall_y) {
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
-            a_w += 3.f * wgt(i) * (0.5f * aCy[i] * __ldg(A.lF + n) - 0.5f * aCx[i] * __ldg(A.lF + pl + n));
+            for (int i = 1; i < 9; ++i) {
+                const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
+                a_w += 3.f * wgt(i) * (0.5f * aCy[i] * __ldg(A.lF + n) - 0.5f * aCx[i] * __ldg(A.lF + pl + n));
+            }
+            a_ws1 = a_w;
+            a_ws2 = -a_w;
+        } else {
+            int px[9], py[9];
+            const int ns = standins(P, x, y, px, py);
+            for (int s = 0; s < ns; ++s) {
+                const bool fx = px[s] < 0 || px[s] >= P.nx, fy = py[s] < 0 || py[s] >= P.ny;
+                float aw = 0.f;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const int zx = px[s] - aCx[i], zy = py[s] - aCy[i];
+                    if (beyond_wall(P, zx, zy)) continue;
+                    const unsigned n = wrap_node(zx, zy, P.nx, P.ny);
+                    aw += 3.f * wgt(i) * (0.5f * aCy[i] * __ldg(A.lF + n) - 0.5f * aCx[i] * __ldg(A.lF + pl + n));
+                }
+                a_ws1 += w_sign1(fx, fy) * aw;
+                a_ws2 += w_sign2(fx, fy) * aw;
+            }
         }
         const float upx = __ldg(P.uin + k), upy = __ldg(P.uin + pl + k);
         const float mphx = __ldg(T.mphi + k), mphy = __ldg(T.mphi + pl + k);
-        // w = mx uy - ux my (previous velocity)
-        const float a_mx = __ldg(A.lmphi + k) + a_w * upy;
-        const float a_my = __ldg(A.lmphi + pl + k) - a_w * upx;
+        // w = s1 mx uy + s2 ux my (previous velocity)
+        const float a_mx = __ldg(A.lmphi + k) + a_ws1 * upy;
+        const float a_my = __ldg(A.lmphi + pl + k) + a_ws2 * upx;
         // the values this pass updates, loaded before its first store (the
         // compiler may not move a load across a store to another field)
         const float lux = A.lu_in[k], luy = A.lu_in[pl + k];
@@ -692,8 +778,8 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
             A.lgrad[(size_t)(2 * p) * pl + k] = a_gx[p] - a_gx[NS];
             A.lgrad[(size_t)(2 * p + 1) * pl + k] = a_gy[p] - a_gy[NS];
         }
-        A.lu_in[k] = lux + -a_w * mphy;
-        A.lu_in[pl + k] = luy + a_w * mphx;
+        A.lu_in[k] = lux + a_ws2 * mphy;
+        A.lu_in[pl + k] = luy + a_ws1 * mphx;
         A.gacc[(size_t)NP * pl + k] = gM + (double)dM;
     }
 }
@@ -713,10 +799,25 @@ __device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjF
             const float *lgx = A.lgrad + (size_t)(2 * p) * pl, *lgy = A.lgrad + (size_t)(2 * p + 1) * pl;
             const float *ll = A.llap + (size_t)p * pl;
             float a = __ldg(A.lphi_pw + (size_t)p * pl + k) - 6.f * (1.f - 4.f / 9.f) * __ldg(ll + k);
+            if (!P.wall_x && !P.wall_y) {
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
-                a += 3.f * wgt(i) * (aCx[i] * __ldg(lgx + n) + aCy[i] * __ldg(lgy + n)) + 6.f * wgt(i) * __ldg(ll + n);
+                for (int i = 1; i < 9; ++i) {
+                    const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
+                    a += 3.f * wgt(i) * (aCx[i] * __ldg(lgx + n) + aCy[i] * __ldg(lgy + n)) + 6.f * wgt(i) * __ldg(ll + n);
+                }
+            } else {
+                // phi of this node also stands at its ghosts beyond the walls
+                int px[9], py[9];
+                const int ns = standins(P, x, y, px, py);
+                for (int s = 0; s < ns; ++s)
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        const int zx = px[s] - aCx[i], zy = py[s] - aCy[i];
+                        if (beyond_wall(P, zx, zy)) continue;
+                        const unsigned n = wrap_node(zx, zy, P.nx, P.ny);
+                        a += 3.f * wgt(i) * (aCx[i] * __ldg(lgx + n) + aCy[i] * __ldg(lgy + n)) +
+                             6.f * wgt(i) * __ldg(ll + n);
+                    }
             }
             A.lphi_tot[(size_t)p * pl + k] = a;
         }
@@ -735,13 +836,17 @@ __device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFiel
         const int x = k % P.nx, y = k / P.nx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const unsigned n = wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny);
+            // f*_i here was pulled by the node at x + c_i, or, where that is
+            // beyond a wall, bounced back into this node as direction opp(i)
+            const bool bb = beyond_wall(P, x + aCx[i], y + aCy[i]);
+            const unsigned n = bb ? k : wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny);
+            const int d = bb ? aOpp[i] : i;
 #pragma unroll
             for (int p = 0; p < NS; ++p)
                 A.lf_in[((size_t)p * 9 + i) * pl + k] = __ldg(A.lphi_tot + (size_t)p * pl + n) +
-                                                        aCx[i] * __ldg(A.lj + (size_t)(2 * p) * pl + n) +
-                                                        aCy[i] * __ldg(A.lj + (size_t)(2 * p + 1) * pl + n);
-            if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = __ldg(A.lg_pull + (size_t)(i - 1) * pl + n);
+                                                        aCx[d] * __ldg(A.lj + (size_t)(2 * p) * pl + n) +
+                                                        aCy[d] * __ldg(A.lj + (size_t)(2 * p + 1) * pl + n);
+            if (i > 0) A.lg_in[(size_t)(i - 1) * pl + k] = __ldg(A.lg_pull + (size_t)(d - 1) * pl + n);
         }
     }
 }

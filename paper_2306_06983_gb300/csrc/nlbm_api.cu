@@ -1102,8 +1102,10 @@ nlbm_status adj_layout(const nlbm_params *p, int nsteps, int every, AdjLayout *L
 {
     nlbm_status st = validate(p, nullptr, err);
     if (st != NLBM_OK) return st;
-    if (p->bc_x != NLBM_BC_PERIODIC || p->bc_y != NLBM_BC_PERIODIC || p->storage != NLBM_STORE_F32) {
-        set_err(err, "the adjoint covers a periodic lattice with FP32 storage");
+    bool wet = false;
+    for (int a = 0; p->wall_cos && a < 2 * (p->n_phases - 1); ++a) wet = wet || p->wall_cos[a] != 0.0;
+    if (p->storage != NLBM_STORE_F32 || wet) {
+        set_err(err, "the adjoint covers FP32 storage and walls without wetting (contact angles of 90 degrees)");
         return NLBM_ENOTSUP;
     }
     if (nsteps < 1 || every < 1) { set_err(err, "nsteps and checkpoint interval must be >= 1"); return NLBM_EINVAL; }

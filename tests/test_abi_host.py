@@ -122,14 +122,15 @@ def test_gravity_and_wetting_walls_are_accepted(lib):
 
 
 def test_adjoint_scope_models_and_boundaries(lib):
-    """Both models and gravity are accepted; walls and 16-bit storage are
-    refused."""
+    """Both models, gravity and walls without wetting are accepted; wetting
+    walls and 16-bit storage are refused."""
     from paper_2306_06983_gb300 import nlbm
     p, _ = W.adjoint_problem(32, 32)
     a = nlbm.nlbm_adjoint_workspace_bytes(dict(p, model="A", model_a_n=1.5), 10, 5)
     assert a == nlbm.nlbm_adjoint_workspace_bytes(p, 10, 5)
     assert a == nlbm.nlbm_adjoint_workspace_bytes(dict(p, gx=1e-5, gy=-2e-5), 10, 5)
-    for bad in (dict(p, wall_y=True), dict(p, wall_x=True), dict(p, storage="bf16")):
+    assert a == nlbm.nlbm_adjoint_workspace_bytes(dict(p, wall_x=True, wall_y=True), 10, 5)
+    for bad in (dict(p, wall_y=True, wall_cos=[0.3, -0.2, 0.0, 0.0]), dict(p, storage="bf16")):
         with pytest.raises(nlbm.NlbmError) as ei:
             nlbm.nlbm_adjoint_workspace_bytes(bad, 10, 5)
         assert ei.value.status == 4
