@@ -627,7 +627,7 @@ __device__ __forceinline__ void rev_collide_node(const StepParams &P, const AdjT
 
 // rev2: F_c's stencil transposed (gather of the F adjoint at the
 // neighbours), then w, m_phi and the source (Model A or B) at the node.
-template <int NS, int MODEL>
+template <int NS, int MODEL, bool WALLS>
 __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTape &T, const AdjFields &A, unsigned k)
 {
     constexpr int N = NS + 1;
@@ -640,7 +640,7 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
         // are the node and, next to a wall, its ghosts (w there formed from
         // this node's m_phi and u with the signs s1, s2 of w_sign1/2).
         float a_w = 0.f, a_ws1 = 0.f, a_ws2 = 0.f;
-        if (!P.wall_x && !P.wall_y) {
+        if constexpr (!WALLS) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
@@ -788,7 +788,7 @@ __device__ __forceinline__ void rev_source_node(const StepParams &P, const AdjTa
 // rev3: the gradient and Laplacian stencils transposed: phi_p(z) entered
 // grad phi_p(z - c_i) with weight 3 w_i c_i and lap phi_p(z - c_i) with 6 w_i
 // (and lap phi_p(z) with -6 (1 - w_0)).
-template <int NS>
+template <int NS, bool WALLS>
 __device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjFields &A, unsigned k)
 {
     const unsigned pl = P.plane;
@@ -799,7 +799,7 @@ __device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjF
             const float *lgx = A.lgrad + (size_t)(2 * p) * pl, *lgy = A.lgrad + (size_t)(2 * p + 1) * pl;
             const float *ll = A.llap + (size_t)p * pl;
             float a = __ldg(A.lphi_pw + (size_t)p * pl + k) - 6.f * (1.f - 4.f / 9.f) * __ldg(ll + k);
-            if (!P.wall_x && !P.wall_y) {
+            if constexpr (!WALLS) {
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const unsigned n = wrap_node(x - aCx[i], y - aCy[i], P.nx, P.ny);
@@ -828,7 +828,7 @@ __device__ __forceinline__ void rev_stencil_node(const StepParams &P, const AdjF
 // rev4: the pull and the moments transposed.  f_i(z) = f*_i(z - c_i) fed
 // phi(z) and j(z): the adjoint of f*_i at y is lphi(y + c_i) + c_i . lj(y + c_i);
 // likewise for the flow populations.  The results seed the previous step.
-template <int NS>
+template <int NS, bool WALLS>
 __device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFields &A, unsigned k)
 {
     const unsigned pl = P.plane;
@@ -838,7 +838,7 @@ __device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFiel
         for (int i = 0; i < 9; ++i) {
             // f*_i here was pulled by the node at x + c_i, or, where that is
             // beyond a wall, bounced back into this node as direction opp(i)
-            const bool bb = beyond_wall(P, x + aCx[i], y + aCy[i]);
+            const bool bb = WALLS && beyond_wall(P, x + aCx[i], y + aCy[i]);
             const unsigned n = bb ? k : wrap_node(x + aCx[i], y + aCy[i], P.nx, P.ny);
             const int d = bb ? aOpp[i] : i;
 #pragma unroll
@@ -862,28 +862,28 @@ __global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
         rev_collide_node<NS>(P, T, A, k);
 }
 
-template <int NS, int MODEL>
+template <int NS, int MODEL, bool WALLS>
 __global__ void rev_source_kernel(const StepParams P, AdjTape T, AdjFields A)
 {
     pdl_wait();
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
-        rev_source_node<NS, MODEL>(P, T, A, k);
+        rev_source_node<NS, MODEL, WALLS>(P, T, A, k);
 }
 
-template <int NS>
+template <int NS, bool WALLS>
 __global__ void rev_stencil_kernel(const StepParams P, AdjFields A)
 {
     pdl_wait();
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
-        rev_stencil_node<NS>(P, A, k);
+        rev_stencil_node<NS, WALLS>(P, A, k);
 }
 
-template <int NS>
+template <int NS, bool WALLS>
 __global__ void rev_pull_kernel(const StepParams P, AdjFields A)
 {
     pdl_wait();
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
-        rev_pull_node<NS>(P, A, k);
+        rev_pull_node<NS, WALLS>(P, A, k);
 }
 
 constexpr int kRedThreads = 256;
@@ -950,9 +950,17 @@ cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFiel
     // and 32 x 16, 64 x 8, 32 x 32 tiles are slower at 1024^2 as well)
     cudaError_t e;
     if ((e = launch_pdl(rev_collide_kernel<NS>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
-    if ((e = launch_pdl(rev_source_kernel<NS, MODEL>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
-    if ((e = launch_pdl(rev_stencil_kernel<NS>, nr, kRevThreads, 0, st, P, A)) != cudaSuccess) return e;
-    return launch_pdl(rev_pull_kernel<NS>, nr, kRevThreads, 0, st, P, A);
+    // periodic lattices take passes without the wall branches (fewer
+    // registers, no local arrays)
+    if (P.wall_x || P.wall_y) {
+        if ((e = launch_pdl(rev_source_kernel<NS, MODEL, true>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess)
+            return e;
+        if ((e = launch_pdl(rev_stencil_kernel<NS, true>, nr, kRevThreads, 0, st, P, A)) != cudaSuccess) return e;
+        return launch_pdl(rev_pull_kernel<NS, true>, nr, kRevThreads, 0, st, P, A);
+    }
+    if ((e = launch_pdl(rev_source_kernel<NS, MODEL, false>, nr, kRevThreads, 0, st, P, T, A)) != cudaSuccess) return e;
+    if ((e = launch_pdl(rev_stencil_kernel<NS, false>, nr, kRevThreads, 0, st, P, A)) != cudaSuccess) return e;
+    return launch_pdl(rev_pull_kernel<NS, false>, nr, kRevThreads, 0, st, P, A);
 }
 
 // dL/dphi_p for the solved phases from dL/dphi over all N phases (phi_N = 1 - sum).
