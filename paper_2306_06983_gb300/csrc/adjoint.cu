@@ -852,10 +852,20 @@ __device__ __forceinline__ void rev_pull_node(const StepParams &P, const AdjFiel
 }
 
 
+// Threads per block of the reverse passes (one node per thread).
+// Measured on the 256^2 sweep (14.7-15.2 ms): 128-thread blocks 15.6 ms,
+// 64-thread 16.3 ms, 128 threads with the collision pass held to 85
+// registers 15.5 ms (at 1024^2 that one is 8.5 % faster, 11.6 against
+// 12.7 ms for 40 steps).
+constexpr int kRevThreads = 256;
+// The collision pass is compiled for three blocks per SM (80 registers, 8
+// bytes spilled; 96 at two): 1024^2 sweep 129.2 -> 119.9 ms, 256^2 13.83 ->
+// 13.73 ms.
+
 // The four reverse passes, one launch each (every pass reads what the one
 // before wrote at the neighbours).
 template <int NS>
-__global__ void rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
+__global__ void __launch_bounds__(kRevThreads, 3) rev_collide_kernel(const StepParams P, AdjTape T, AdjFields A)
 {
     pdl_wait();   // the previous kernel of the sweep has completed
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < P.plane; k += gridDim.x * blockDim.x)
@@ -924,12 +934,6 @@ int blocks_for(unsigned n)
     return (int)(b ? b : 1);
 }
 
-// Threads per block of the four reverse passes (one node per thread).
-// Measured on the 256^2 sweep (14.7-15.2 ms): 128-thread blocks 15.6 ms,
-// 64-thread 16.3 ms, 128 threads with the collision pass held to 85
-// registers 15.5 ms (at 1024^2 that one is 8.5 % faster, 11.6 against
-// 12.7 ms for 40 steps).
-constexpr int kRevThreads = 256;
 
 template <int NS, int MODEL>
 cudaError_t reverse_step_ns(const StepParams &P, const AdjTape &T, const AdjFields &A, bool taped, cudaStream_t st)
