@@ -1157,22 +1157,6 @@ cudaError_t adj_save_state(nlbm_adjoint *a, float *dst)
     return cudaSuccess;
 }
 
-cudaError_t adj_load_state(nlbm_adjoint *a, const float *src)
-{
-    nlbm_sim *s = a->sim;
-    const size_t pl = a->plane, pb = sizeof(float) * pl;
-    s->cur = 0;
-    struct Part { void *dst; size_t n; } parts[] = {
-        {s->f(0), pb * 9 * a->ns}, {s->g(0), pb * 8}, {s->u(0), pb * 2}, {s->phi(0), pb * a->ns}, {s->mphi(), pb * 2}};
-    const char *d = (const char *)src;
-    for (const Part &p : parts) {
-        cudaError_t e = cudaMemcpyAsync(p.dst, d, p.n, cudaMemcpyDeviceToDevice, a->stream);
-        if (e != cudaSuccess) return e;
-        d += p.n;
-    }
-    return cudaSuccess;
-}
-
 // Step parameters whose inputs are a packed state record.
 StepParams adj_params_from_state(const nlbm_adjoint *a, const float *state)
 {
