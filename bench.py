@@ -619,7 +619,6 @@ def run_gpu(args):
             sim.set_tile(*args.tile)
         else:
             sim.autotune(20)
-        sim.step(args.warmup)
         stream.synchronize()
 
         # ---------------------------------------------- device-timed region
@@ -628,18 +627,21 @@ def run_gpu(args):
         # is one launch, so the region's time / K is the kernel's average
         # launch duration (an event between launches would stop each launch
         # from overlapping the tail of the one before)
+        # the clock sampler starts (and waits for nvidia-smi) before the W
+        # warm-up steps, so that the GPU is busy right up to the timed region
         e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        launches0 = sim.kernel_launches
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
         with ClockSampler(local) as clocks:
+            sim.step(args.warmup)
+            launches0 = sim.kernel_launches
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
             e_start.record(stream)
             sim.step(args.steps)
             e_end.record(stream)
             torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+            if world > 1:
+                dist.barrier()
         launches = sim.kernel_launches - launches0
         total_ms = e_start.elapsed_time(e_end)
         mass = sim.phase_mass(allow_diverged=True)
